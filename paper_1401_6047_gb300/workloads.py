@@ -1,0 +1,147 @@
+"""Seeded synthetic workloads: parameter sets and random states.
+
+This module holds no arithmetic of the method.  It only names the parameter
+points the solver is run on (the paper's own Table 1 run and the five
+configurations the library is measured on) and draws seeded random inputs,
+so that the CUDA path and the CPU oracle are fed identical data.
+
+Parameter names follow the dimensionless units of the paper's Sec. 2:
+E_dc, E_omega, omega (drive, E(t) = E_dc + E_omega cos(omega t)), B (magnetic
+field), mu = Delta_1 / (2 k_B T), alpha = m / m_x; the phi_y grid holds
+``m_points`` points on [phiy_min, phiy_max] and harmonics run n = 0..n_max.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+FP64 = 0
+FP32_MIXED = 1
+
+
+@dataclass
+class Params:
+    E_dc: float = 1.0
+    E_omega: float = 0.1
+    omega: float = 1.0
+    B: float = 0.0
+    mu: float = 1.0
+    alpha: float = 1.0
+    n_max: int = 30
+    m_points: int = 201
+    phiy_min: float = -10.0
+    phiy_max: float = 10.0
+    dt: float = 1e-3
+    periods: float = 20.0
+    t_max: float = 0.0
+    avg_window: float = 10.0
+    precision: int = FP64
+
+    def replace(self, **kw) -> "Params":
+        return dataclasses.replace(self, **kw)
+
+    @property
+    def cells(self) -> int:
+        return (self.n_max + 1) * self.m_points
+
+
+# --- the five measured configurations ------------------------------------
+
+def c1_fp64() -> Params:
+    """Plain FP64 single instance: n = 0..30, 201 phi_y points on [-10, 10],
+    dt = 1e-3, mu = 1, E_dc = 1, E_omega = 0.1, omega = 1, B = 0, 20 periods,
+    averaged over the last 10."""
+    return Params(E_dc=1.0, E_omega=0.1, omega=1.0, B=0.0, mu=1.0, n_max=30,
+                  m_points=201, phiy_min=-10.0, phiy_max=10.0, dt=1e-3, periods=20.0,
+                  avg_window=10.0, precision=FP64)
+
+
+def c2(precision: int = FP32_MIXED) -> Params:
+    """Single instance, n = 0..400, 4001 points on [-40, 40], dt = 5e-4, mu = 2,
+    E_dc = 2, E_omega = 0.5, omega = 2, B = 4, 50 periods, last 10 averaged."""
+    return Params(E_dc=2.0, E_omega=0.5, omega=2.0, B=4.0, mu=2.0, n_max=400,
+                  m_points=4001, phiy_min=-40.0, phiy_max=40.0, dt=5e-4, periods=50.0,
+                  avg_window=10.0, precision=precision)
+
+
+def c3(precision: int = FP32_MIXED) -> Params:
+    """Low-temperature stress: n = 0..2048, 8193 points on [-80, 80],
+    dt = 2.5e-4, mu = 20, E_dc = 4, E_omega = 1, omega = 3, B = 8, 30 periods,
+    last 10 averaged."""
+    return Params(E_dc=4.0, E_omega=1.0, omega=3.0, B=8.0, mu=20.0, n_max=2048,
+                  m_points=8193, phiy_min=-80.0, phiy_max=80.0, dt=2.5e-4,
+                  periods=30.0, avg_window=10.0, precision=precision)
+
+
+def paper_table1(precision: int = FP32_MIXED) -> Params:
+    """The run timed in the paper's Table 1 (Sec. 7): E_dc = 7, phi_y in
+    [-6, 6] with 4000 points, B = 4, E_omega = 0.1, omega = 10, mu = 116,
+    alpha = 0.9496, 120 harmonics, dt = 1e-4, t = 10 (10^5 steps)."""
+    # 10 time units at omega = 10 is 10 * 10 / (2 pi) periods
+    per = 10.0 * 10.0 / (2.0 * math.pi)
+    return Params(E_dc=7.0, E_omega=0.1, omega=10.0, B=4.0, mu=116.0, alpha=0.9496,
+                  n_max=119, m_points=4000, phiy_min=-6.0, phiy_max=6.0, dt=1e-4,
+                  periods=per, avg_window=1.0, precision=precision)
+
+
+# parameter box of the batched sweep and the surrogate
+SWEEP_BOX = {
+    "E_dc": (0.0, 6.0),
+    "E_omega": (0.01, 1.0),
+    "omega": (0.5, 6.0),
+    "B": (0.0, 6.0),
+    "mu": (0.5, 10.0),
+}
+
+
+def sweep_grid_rule(mu: float, B: float) -> tuple[int, int, float]:
+    """Per-point grid of the batched sweep: phi_y range L = 7/sqrt(mu) + 1.5 B,
+    spacing about 0.02, 201..2001 points; harmonics 20..200 growing with mu
+    and B.  Returns (n_max, m_points, L)."""
+    L = 7.0 / math.sqrt(mu) + 1.5 * B
+    m_points = int(min(max(2 * math.ceil(L / 0.02) + 1, 201), 2001))
+    n_max = int(min(max(math.ceil(12 + 3 * mu + 10 * B), 20), 200))
+    return n_max, m_points, L
+
+
+def sweep_points(n: int = 4096, seed: int = 1401, periods: float = 30.0,
+                 avg_window: float = 10.0, dt: float = 1e-3,
+                 precision: int = FP32_MIXED) -> list[Params]:
+    """Seeded uniform draws over SWEEP_BOX with the per-point grid rule."""
+    rng = np.random.default_rng(seed)
+    cols = {k: rng.uniform(lo, hi, size=n) for k, (lo, hi) in SWEEP_BOX.items()}
+    out = []
+    for i in range(n):
+        mu = float(cols["mu"][i])
+        B = float(cols["B"][i])
+        n_max, m_points, L = sweep_grid_rule(mu, B)
+        out.append(Params(E_dc=float(cols["E_dc"][i]), E_omega=float(cols["E_omega"][i]),
+                          omega=float(cols["omega"][i]), B=B, mu=mu, n_max=n_max,
+                          m_points=m_points, phiy_min=-L, phiy_max=L, dt=dt,
+                          periods=periods, avg_window=avg_window, precision=precision))
+    return out
+
+
+def sweep_matrix(n: int, seed: int) -> np.ndarray:
+    """[n, 5] seeded uniform points (E_dc, E_omega, omega, B, mu) over SWEEP_BOX."""
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.uniform(lo, hi, size=n) for (lo, hi) in SWEEP_BOX.values()],
+                    axis=1)
+
+
+def random_state(p: Params, seed: int, scale: float = 1.0, parity: int | None = None):
+    """Four seeded random arrays [n_max+1][m_points] (a_w, b_w, a_f, b_f) with
+    b_0 = 0.  ``parity`` = 0 or 1 keeps only cells with (n+m) % 2 == parity."""
+    rng = np.random.default_rng(seed)
+    shp = (p.n_max + 1, p.m_points)
+    arrs = [scale * rng.standard_normal(shp) for _ in range(4)]
+    arrs[1][0, :] = 0.0
+    arrs[3][0, :] = 0.0
+    if parity is not None:
+        n, m = np.indices(shp)
+        mask = ((n + m) % 2) == parity
+        arrs = [np.where(mask, x, 0.0) for x in arrs]
+    return arrs

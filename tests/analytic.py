@@ -1,0 +1,112 @@
+"""Closed forms and independent integrators used to pin the oracle.
+
+Nothing here shares arithmetic with the oracle or the CUDA library.  Each
+function is derived from the continuum equation of the paper (Sec. 2,
+Eq. boltzmann_final) by a route other than the finite-difference scheme.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.special as sp
+
+
+def xi(x):
+    """Esaki-Tsu shape x/(1+x^2) (Sec. 4, Eq. xi_def)."""
+    return x / (1.0 + x * x)
+
+
+def bessel_ratio(mu: float, n: int | np.ndarray):
+    """I_n(mu)/I_0(mu) from scipy's exponentially scaled I_n."""
+    return sp.ive(n, mu) / sp.ive(0, mu)
+
+
+def esaki_tsu(E: float, mu: float) -> float:
+    """Stationary drift velocity at B = 0 and constant E:
+    v = (I_1/I_0) E/(1+E^2).  At B = 0 each harmonic obeys
+    da/dt = a0 - a - nE b, db/dt = -b + nE a, whose fixed point for n = 1
+    integrated over phi_y gives this."""
+    return float(bessel_ratio(mu, 1) * xi(E))
+
+
+def tucker_absorption(E_dc: float, E_omega: float, omega: float, nterms: int = 80) -> float:
+    """Absorption A = <2 I_0 v cos(omega t)/I_1> at B = 0 (Eq. absorption_def).
+
+    Solving the n = 1 harmonic equation at B = 0 with the Jacobi-Anger
+    expansion of exp(i (E_omega/omega) sin(omega t)) gives
+        A = sum_k J_k(a) [J_{k+1}(a) + J_{k-1}(a)] xi(E_dc + k omega),
+    a = E_omega/omega.  (The printed Eq. absorption_tacker carries an extra
+    factor 2 I_1/I_0 that is inconsistent with Eq. absorption_def; the
+    definition is followed here.)"""
+    a = E_omega / omega
+    k = np.arange(-nterms, nterms + 1)
+    return float(np.sum(sp.jv(k, a) * (sp.jv(k + 1, a) + sp.jv(k - 1, a)) *
+                        xi(E_dc + k * omega)))
+
+
+def tucker_vdc(E_dc: float, E_omega: float, omega: float, mu: float, nterms: int = 80) -> float:
+    """Time-averaged drift velocity at B = 0: (I_1/I_0) sum_k J_k(a)^2 xi(E_dc + k omega)."""
+    a = E_omega / omega
+    k = np.arange(-nterms, nterms + 1)
+    return float(bessel_ratio(mu, 1) * np.sum(sp.jv(k, a) ** 2 * xi(E_dc + k * omega)))
+
+
+def ktitorov_absorption(E_dc: float, E_omega: float, omega: float) -> float:
+    """Small-signal limit of the Tucker form: A ~ (a/2)[xi(E_dc+omega) - xi(E_dc-omega)]
+    to first order in a = E_omega/omega."""
+    a = E_omega / omega
+    return 0.5 * a * (xi(E_dc + omega) - xi(E_dc - omega))
+
+
+def characteristics_vdc(E: float, B: float, mu: float, nx: int = 128, ny: int = 200,
+                        ds: float = 0.01, smax: float = 25.0, ysig: float = 7.0) -> float:
+    """Stationary drift velocity for constant E and B by the method of
+    characteristics (Sec. 4, Eqs. pendulum_phi_x, pendulum_phi_y and
+    pendulum_drift_velocity, extended to finite temperature).
+
+    The streaming field (E + B phi_y, -B sin phi_x) is divergence free, so the
+    relaxation-time equation is solved exactly by
+        v = int_0^inf e^{-s} < sin Phi_x(s; phi0) >_{f0} ds,
+    Phi(s; phi0) the pendulum trajectory started at phi0 drawn from f0
+    (von Mises(mu) in phi_x, normal with variance 1/mu in phi_y).
+    Midpoint quadrature over phi0, RK4 in s, Simpson in s."""
+    x = 2 * np.pi * (np.arange(nx) + 0.5) / nx - np.pi
+    wx = np.exp(mu * (np.cos(x) - 1.0))
+    wx /= wx.sum()
+    L = ysig / np.sqrt(mu)
+    y = -L + 2 * L * (np.arange(ny) + 0.5) / ny
+    wy = np.exp(-mu * y * y / 2.0)
+    wy /= wy.sum()
+    px, py = np.meshgrid(x, y, indexing="ij")
+    w = np.outer(wx, wy)
+
+    def f(px, py):
+        return E + B * py, -B * np.sin(px)
+
+    ns = int(round(smax / ds))
+    ns += ns % 2
+    vals = np.empty(ns + 1)
+    vals[0] = np.sum(w * np.sin(px))
+    for i in range(ns):
+        k1 = f(px, py)
+        k2 = f(px + 0.5 * ds * k1[0], py + 0.5 * ds * k1[1])
+        k3 = f(px + 0.5 * ds * k2[0], py + 0.5 * ds * k2[1])
+        k4 = f(px + ds * k3[0], py + ds * k3[1])
+        px = px + ds / 6 * (k1[0] + 2 * k2[0] + 2 * k3[0] + k4[0])
+        py = py + ds / 6 * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1])
+        vals[i + 1] = np.sum(w * np.sin(px))
+    g = np.exp(-ds * np.arange(ns + 1)) * vals
+    return float(ds / 3 * (g[0] + g[-1] + 4 * g[1:-1:2].sum() + 2 * g[2:-1:2].sum()))
+
+
+def f0_fourier(mu: float, alpha: float, nmax: int, phiy: np.ndarray, nx: int = 1024) -> np.ndarray:
+    """Fourier cosine coefficients a0_n(phi_y) of the closed-form equilibrium
+    f0 = exp(mu cos phi_x - mu phi_y^2/2) sqrt(mu/(2 pi alpha)) / (2 pi I_0(mu))
+    (Eq. Bolzmann_initial_pdf), by FFT of f0 sampled in phi_x: the series
+    f0 = sum_n a0_n cos(n phi_x) of Eq. f0_fourier."""
+    x = 2 * np.pi * np.arange(nx) / nx
+    # exp(mu cos x)/I_0(mu) = exp(mu (cos x - 1)) / ive(0, mu)
+    fx = np.exp(mu * (np.cos(x) - 1.0)) / sp.ive(0, mu)
+    c = np.fft.rfft(fx).real / nx       # c_k with fx = c_0 + 2 sum_k c_k cos(kx)
+    coef = np.concatenate([[c[0]], 2 * c[1:nmax + 1]])
+    gy = np.sqrt(mu / (2 * np.pi * alpha)) * np.exp(-mu * phiy ** 2 / 2) / (2 * np.pi)
+    return np.outer(coef, gy)

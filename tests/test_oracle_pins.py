@@ -1,0 +1,334 @@
+"""Pins of the FP64 oracle to facts that do not come from the oracle itself.
+
+Each ``pin_*`` function runs the oracle (optionally with a planted mistake)
+and returns the worst normalised error (error / tolerance); the pin holds when
+it is <= 1.  ``test_planted_mistakes_are_caught`` shows that every planted
+mistake of the oracle breaks at least one pin.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_6047_gb300 import workloads as W
+from tests import analytic as an
+
+
+def _rel(x, ref):
+    return abs(x - ref) / abs(ref)
+
+
+# --- Bessel ratios and the equilibrium ----------------------------------
+
+def test_bessel_ratio_matches_scipy():
+    """I_n/I_0 (Sec. 2, Eq. Bolzmann_initial_pdf) against scipy.special.ive."""
+    for mu, nmax in [(0.5, 40), (2.0, 60), (20.0, 200), (116.0, 400), (1.0, 2048)]:
+        r = oracle.bessel_ratio(mu, nmax)
+        ref = an.bessel_ratio(mu, np.arange(nmax + 1))
+        assert np.max(np.abs(r - ref)) < 1e-14, (mu, nmax)
+        assert r[0] == 1.0
+
+
+def test_bessel_ratio_recurrence():
+    """I_{n-1} - I_{n+1} = (2n/mu) I_n, a property of the exact functions."""
+    mu = 7.5
+    r = oracle.bessel_ratio(mu, 50)
+    n = np.arange(1, 40)
+    assert np.max(np.abs(r[n - 1] - r[n + 1] - 2 * n / mu * r[n])) < 1e-14
+
+
+def pin_equilibrium(flags=0):
+    p = W.Params(mu=2.5, alpha=0.9496, n_max=12, m_points=241, phiy_min=-6, phiy_max=6)
+    a0 = oracle.equilibrium(p, flags)
+    phi = np.linspace(p.phiy_min, p.phiy_max, p.m_points)
+    ref = an.f0_fourier(p.mu, p.alpha, p.n_max, phi)
+    err_coef = np.max(np.abs(a0 - ref)) / np.max(np.abs(ref)) / 1e-13
+    # normalisation Eq. norm_in_phi: 2 pi sqrt(alpha) int a0_0 dphi = 1
+    dphi = phi[1] - phi[0]
+    nrm = 2 * math.pi * math.sqrt(p.alpha) * dphi * a0[0].sum()
+    return max(err_coef, abs(nrm - 1) / 1e-12)
+
+
+def test_equilibrium_is_fourier_series_of_f0():
+    """a0_n equals the FFT of the closed-form f0 in phi_x, and is normalised."""
+    assert pin_equilibrium() <= 1
+
+
+# --- B = 0 closed forms --------------------------------------------------
+
+def pin_esaki_tsu(flags=0):
+    """B = 0, E constant: the Crank-Nicolson fixed point is the continuum fixed
+    point, so after t = 30 the drift velocity is Esaki-Tsu to roundoff."""
+    worst = 0.0
+    for E in (0.3, 1.0, 2.5):
+        p = W.Params(E_dc=E, E_omega=0.0, omega=0.0, B=0.0, mu=1.3, n_max=6, m_points=121,
+                     phiy_min=-9, phiy_max=9, dt=2e-3, t_max=32.0, avg_window=1.0)
+        r = oracle.solve(p, flags)
+        worst = max(worst, _rel(r.v_dc, an.esaki_tsu(E, p.mu)) / 1e-11)
+    return worst
+
+
+def test_esaki_tsu():
+    assert pin_esaki_tsu() <= 1
+
+
+def pin_tucker(flags=0):
+    """The 31 x 201 FP64 configuration (B = 0): absorption against the Tucker
+    form and the time-averaged drift against its companion series.  The
+    scheme is second order in dt, dt = 1e-3 -> relative error ~1e-7."""
+    p = W.c1_fp64()
+    r = oracle.solve(p, flags)
+    eA = _rel(r.A, an.tucker_absorption(p.E_dc, p.E_omega, p.omega)) / 1e-6
+    ev = _rel(r.v_dc, an.tucker_vdc(p.E_dc, p.E_omega, p.omega, p.mu)) / 1e-8
+    en = r.norm_err / 1e-12
+    return max(eA, ev, en)
+
+
+def test_tucker_absorption_and_vdc():
+    assert pin_tucker() <= 1
+
+
+def test_ktitorov_small_signal():
+    """Small-signal limit: within O(a^2) (a = 0.1) of the Ktitorov form."""
+    p = W.c1_fp64().replace(periods=14.0, avg_window=4.0)
+    r = oracle.solve(p)
+    k = an.ktitorov_absorption(p.E_dc, p.E_omega, p.omega)
+    assert _rel(r.A, k) < 2e-2
+    # the sign: at E_dc = 1 < ... the small-signal absorption here is positive
+    assert r.A > 0
+
+
+def test_tucker_negative_absorption_region():
+    """Gain (A < 0) at E_dc > 1 with omega < E_dc, matching the Tucker sign."""
+    p = W.c1_fp64().replace(E_dc=3.0, omega=1.5, E_omega=0.3, n_max=8, m_points=101,
+                            periods=12.0, avg_window=4.0, dt=2e-3)
+    r = oracle.solve(p)
+    t = an.tucker_absorption(p.E_dc, p.E_omega, p.omega)
+    assert t < 0 and r.A < 0
+    assert _rel(r.A, t) < 1e-5
+
+
+def pin_relaxation(flags=0):
+    """E = 0, B = 0: every cell relaxes geometrically toward a0,
+    z_k - z_eq = ((1 - h/2)/(1 + h/2))^k (z_0 - z_eq) on both grids."""
+    p = W.Params(E_dc=0.0, E_omega=0.0, omega=0.0, B=0.0, mu=1.7, n_max=5, m_points=41,
+                 phiy_min=-5, phiy_max=5, dt=0.01, t_max=5.0, avg_window=1.0)
+    a0 = oracle.equilibrium(p)
+    aw, bw, af, bf = W.random_state(p, seed=7)
+    st = oracle.State(aw.copy(), bw.copy(), af.copy(), bf.copy())
+    k = 150
+    oracle.advance(p, st, 0, k, flags)
+    h = p.dt
+    q = ((1 - h / 2) / (1 + h / 2)) ** k
+    worst = 0.0
+    for got, z0, eq in ((st.aw, aw, a0), (st.bw, bw, 0 * a0), (st.af, af, a0), (st.bf, bf, 0 * a0)):
+        worst = max(worst, np.max(np.abs((got - eq) - q * (z0 - eq))) / 1e-13)
+    return worst
+
+
+def test_relaxation_closed_form():
+    assert pin_relaxation() <= 1
+
+
+# --- E = 0, B != 0: f0 is stationary -----------------------------------
+
+def _stationary_dev(m_points, flags=0, alpha=0.9496):
+    p = W.Params(E_dc=0.0, E_omega=0.0, omega=0.0, B=2.0, mu=2.0, alpha=alpha, n_max=16,
+                 m_points=m_points, phiy_min=-7, phiy_max=7, dt=5e-3, t_max=3.0,
+                 avg_window=1.0)
+    st = oracle.init(p, flags)
+    a0 = oracle.equilibrium(p)
+    oracle.advance(p, st, 0, 600, flags)
+    scale = np.max(np.abs(a0))
+    return max(np.max(np.abs(st.aw - a0)), np.max(np.abs(st.bw))) / scale
+
+
+def pin_stationary(flags=0):
+    """The streaming term annihilates f0 when E = 0 (I_{n-1} - I_{n+1} =
+    (2n/mu) I_n), so the discrete state stays at a0 up to the O(dphi^2)
+    truncation of the central differences: halving dphi divides the
+    deviation by ~4."""
+    d1 = _stationary_dev(141, flags)
+    d2 = _stationary_dev(281, flags)
+    ratio = d1 / max(d2, 1e-300)
+    return max(d1 / 2e-3, abs(ratio - 4.0) / 0.4)
+
+
+def test_equilibrium_stationary_at_zero_field():
+    assert pin_stationary() <= 1
+
+
+# --- invariants ------------------------------------------------------------
+
+def pin_norm(flags=0):
+    """Norm (Eq. norm_in_phi) is conserved at B != 0 and E(t) != 0 when the
+    grid edges carry no density: the n = 0 update telescopes in m."""
+    p = W.Params(E_dc=1.5, E_omega=0.7, omega=2.0, B=1.5, mu=2.0, n_max=20, m_points=161,
+                 phiy_min=-8, phiy_max=8, dt=4e-3, periods=3.0, avg_window=1.0)
+    r = oracle.solve(p, flags)
+    return r.norm_err / 1e-12
+
+
+def test_norm_conserved():
+    assert pin_norm() <= 1
+
+
+def _sym_run(E_dc, E_om, B, flags=0):
+    p = W.Params(E_dc=E_dc, E_omega=E_om, omega=1.7, B=B, mu=1.5, n_max=14, m_points=121,
+                 phiy_min=-7, phiy_max=7, dt=5e-3, periods=2.0, avg_window=1.0)
+    return oracle.solve(p, flags)
+
+
+def pin_symmetry(flags=0):
+    """On a grid symmetric about phi_y = 0: (E_dc, E_omega) -> -(E_dc, E_omega)
+    maps f(phi_x, phi_y) to f(-phi_x, -phi_y), so v(t) -> -v(t);
+    B -> -B maps f to f(phi_x, -phi_y), so v(t) is unchanged."""
+    r0 = _sym_run(1.2, 0.8, 1.3, flags)
+    r1 = _sym_run(-1.2, -0.8, 1.3, flags)
+    r2 = _sym_run(1.2, 0.8, -1.3, flags)
+    s = np.max(np.abs(r0.v))
+    e1 = np.max(np.abs(r0.v + r1.v)) / s / 1e-12
+    e2 = np.max(np.abs(r0.v - r2.v)) / s / 1e-12
+    return max(e1, e2)
+
+
+def test_symmetries():
+    assert pin_symmetry() <= 1
+
+
+def pin_sublattice(flags=0):
+    """T at (n, m) reads (n, m) and (n +- 1, m +- 1) only, so the two
+    sublattices n+m even / odd never exchange data: two runs that differ only
+    on the even sublattice agree exactly on the odd one."""
+    p = W.Params(E_dc=0.7, E_omega=0.4, omega=1.1, B=2.2, mu=1.5, n_max=9, m_points=37,
+                 phiy_min=-4, phiy_max=4, dt=1e-2, periods=1.0, avg_window=1.0)
+    base = W.random_state(p, seed=3)
+    pert = W.random_state(p, seed=4, parity=0)
+    s1 = oracle.State(*(x.copy() for x in base))
+    s2 = oracle.State(*(x + y for x, y in zip(base, pert)))
+    oracle.advance(p, s1, 0, 40, flags)
+    oracle.advance(p, s2, 0, 40, flags)
+    n, m = np.indices(base[0].shape)
+    odd = ((n + m) % 2) == 1
+    d = max(np.max(np.abs(getattr(s1, k) - getattr(s2, k))[odd]) for k in ("aw", "bw", "af", "bf"))
+    return 0.0 if d == 0.0 else 1e30
+
+
+def test_sublattice_decoupling():
+    assert pin_sublattice() == 0.0
+
+
+# --- convergence order -----------------------------------------------------
+
+def _conv_params(**kw):
+    base = dict(E_dc=1.0, E_omega=0.5, omega=math.pi, B=1.0, mu=2.0, n_max=24, m_points=161,
+                phiy_min=-8, phiy_max=8, dt=5e-3, periods=8.0, avg_window=2.0)
+    base.update(kw)
+    return W.Params(**base)
+
+
+def _order(x1, x2, x3):
+    return math.log2(abs(x1 - x2) / abs(x2 - x3))
+
+
+def pin_order_dt(flags=0):
+    """Crank-Nicolson + staggered leap-frog is second order in dt."""
+    rs = [oracle.solve(_conv_params(dt=d), flags) for d in (1e-2, 5e-3, 2.5e-3)]
+    oA = _order(*(r.A for r in rs))
+    ov = _order(*(r.v_dc for r in rs))
+    return max(abs(oA - 2.0), abs(ov - 2.0)) / 0.2
+
+
+def test_second_order_in_dt():
+    assert pin_order_dt() <= 1
+
+
+def pin_order_dphi(flags=0):
+    """Central differences in phi_y: second order in dphi, seen in the
+    time-averaged drift and in the sup norm of the drift-velocity trace (the
+    absorption at these parameters is almost insensitive to dphi, so its
+    differences are not yet asymptotic)."""
+    rs = [oracle.solve(_conv_params(m_points=mp), flags) for mp in (81, 161, 321)]
+    ov = _order(*(r.v_dc for r in rs))
+    d1 = np.max(np.abs(rs[0].v - rs[1].v))
+    d2 = np.max(np.abs(rs[1].v - rs[2].v))
+    ot = math.log2(d1 / d2)
+    return max(abs(ov - 2.0), abs(ot - 2.0)) / 0.2
+
+
+def test_second_order_in_dphi():
+    assert pin_order_dphi() <= 1
+
+
+# --- B != 0: the method of characteristics ------------------------------------
+
+_CHAR_CACHE = {}
+
+
+def pin_characteristics(flags=0):
+    """Constant E and B != 0: the stationary drift velocity from the oracle,
+    Richardson-extrapolated in dphi, equals the characteristics integral."""
+    E, B, mu = 1.0, 1.0, 3.0
+    if "v" not in _CHAR_CACHE:
+        _CHAR_CACHE["v"] = an.characteristics_vdc(E, B, mu)
+    ref = _CHAR_CACHE["v"]
+    vs = []
+    for mp in (321, 641):
+        p = W.Params(E_dc=E, E_omega=0.0, omega=0.0, B=B, mu=mu, alpha=0.9496, n_max=24,
+                     m_points=mp, phiy_min=-8, phiy_max=8, dt=2e-3, t_max=25.0,
+                     avg_window=1.0)
+        vs.append(oracle.solve(p, flags).v_dc)
+    v_ex = vs[1] - (vs[0] - vs[1]) / 3.0
+    return _rel(v_ex, ref) / 2e-5
+
+
+def test_characteristics_dc_at_finite_B():
+    assert pin_characteristics() <= 1
+
+
+# --- window arithmetic -------------------------------------------------------
+
+def test_window_of_pure_cosine():
+    """A trace v_k = cos(omega t_k) has <v cos> = 1/2 and <v> = 0 over whole
+    periods, so A = (2 I_0/I_1)/2."""
+    p = W.c1_fp64().replace(periods=3.0, avg_window=2.0)
+    dt, P, K, Kw = oracle.time_grid(p)
+    assert P == round(2 * math.pi / (p.omega * p.dt))
+    assert abs(dt * P * p.omega - 2 * math.pi) < 1e-12
+    assert K == 3 * P and Kw == 2 * P
+    t = dt * np.arange(K + 1)
+    v = np.cos(p.omega * t)
+    A, vb = oracle.window(p, v)
+    assert abs(A - 1.0 / an.bessel_ratio(p.mu, 1)) < 1e-12
+    assert abs(vb) < 1e-12
+
+
+def test_rejects_invalid_parameters():
+    bad = [dict(n_max=0), dict(m_points=2), dict(dt=0.0), dict(mu=-1.0),
+           dict(omega=-1.0), dict(E_dc=float("nan")), dict(avg_window=30.0)]
+    for kw in bad:
+        with pytest.raises(ValueError):
+            oracle.solve(W.c1_fp64().replace(**kw))
+
+
+# --- every planted mistake is caught ----------------------------------------
+
+MUTATIONS = {
+    oracle.MUT_PAPER_B_SIGN: [pin_esaki_tsu],
+    oracle.MUT_ALPHA_STENCIL: [pin_stationary, pin_characteristics],
+    oracle.MUT_SIGMA0_ONE: [pin_equilibrium, pin_tucker],
+    oracle.MUT_NO_CHI: [pin_stationary],
+    oracle.MUT_STALE_SOURCE: [pin_order_dt],
+    oracle.MUT_THETA_START_ONLY: [pin_tucker],
+    oracle.MUT_STENCIL_INDEX: [pin_sublattice],
+    oracle.MUT_NO_B0_RESET: [pin_stationary],
+}
+
+
+@pytest.mark.parametrize("flag", sorted(MUTATIONS))
+def test_planted_mistakes_are_caught(flag):
+    for pin in MUTATIONS[flag]:
+        assert pin(0) <= 1, pin.__name__
+        e = pin(flag)
+        assert not (e <= 1), (pin.__name__, flag, e)
