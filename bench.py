@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 superlattice BTE solver.
+
+One benchmark step is one complete solve of the configured workload through
+the C ABI: return to the equilibrium start with the start-up half step
+(bte_reset), every leap-frog step of the run (bte_run: one fused kernel per
+step, replayed from CUDA graphs), and the window reductions
+(bte_observables).  Default workload: the single instance with harmonics
+n = 0..400 and 4001 phi_y points on [-40, 40], dt = 5e-4, 50 drive periods
+(314,150 steps), FP32 state with FP64 reductions.
+
+The metric is cell-updates per second: one cell (n, m) advanced by one full
+dt on both the whole and the fractional grid counts once (the paper's MLUPS
+convention, Sec. 7).
+
+Multi-GPU (torchrun): every rank solves its own replica; value = all ranks'
+cell-updates / the slowest rank's time ("scaling": "weak").  There is no
+data-path collective.
+
+``--impl reference`` times the FP64 CPU oracle instead (a bounded sample of
+the same workload on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s & sweep points/s at ≤1e-5 abs absorption error; % mem roofline"
+UNIT = "cell-updates/s"
+PROFILE_FILE = os.path.join(ROOT, "profiles", "fused_step_c2_fp32.md")
+
+
+def workload(name: str, precision: str):
+    from paper_1401_6047_gb300 import workloads as W
+    prec = W.FP64 if precision == "fp64" else W.FP32_MIXED
+    table = {
+        "c1": (W.c1_fp64().replace(precision=prec),
+               "single instance: n=0..30, 201 phi_y points on [-10,10], dt=1e-3, mu=1, E_dc=1, "
+               "E_omega=0.1, omega=1, B=0, 20 periods"),
+        "c2": (W.c2(prec),
+               "single instance: n=0..400, 4001 phi_y points on [-40,40], dt=5e-4, mu=2, E_dc=2, "
+               "E_omega=0.5, omega=2, B=4, 50 periods, last 10 averaged"),
+        "c3": (W.c3(prec),
+               "low-temperature single instance: n=0..2048, 8193 phi_y points on [-80,80], "
+               "dt=2.5e-4, mu=20, E_dc=4, E_omega=1, omega=3, B=8, 30 periods"),
+        "table1": (W.paper_table1(prec),
+                   "the paper's Table 1 run: 120 harmonics, 4000 phi_y points on [-6,6], "
+                   "dt=1e-4, mu=116, E_dc=7, E_omega=0.1, omega=10, B=4, t=10"),
+    }
+    return table[name]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_sha() -> str:
+    src = os.path.join(ROOT, "paper_1401_6047_gb300", "csrc", "bte_kernels.cu")
+    with open(src, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic(config_key: str):
+    """DRAM bytes per launch of the fused step kernel from the committed ncu
+    summary, or None when the summary is missing or the kernel source changed
+    since it was taken."""
+    try:
+        with open(PROFILE_FILE) as f:
+            txt = f.read()
+    except OSError:
+        return None
+    sha = None
+    val = None
+    for line in txt.splitlines():
+        line = line.strip().strip("-* ")
+        if line.startswith("kernel_sha:"):
+            sha = line.split(":", 1)[1].strip()
+        if line.startswith(f"traffic_bytes_per_launch[{config_key}]:"):
+            try:
+                val = float(line.split(":", 1)[1].strip())
+            except ValueError:
+                val = None
+    if sha != kernel_sha():
+        return None
+    return val
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.uuid and self.uuid not in parts[1]:
+                continue
+            try:
+                sm.append(float(parts[2]))
+                mx.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[6:10]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample(p, target_s: float):
+    """Times the oracle as it stands on a bounded number of steps of workload p;
+    returns (cell-updates/s, threads, steps, seconds)."""
+    import oracle
+    st = oracle.init(p)
+    t0 = time.perf_counter()
+    oracle.advance(p, st, 0, 2)
+    dt2 = time.perf_counter() - t0
+    n = max(2, min(2000, int(target_s / max(dt2 / 2, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.advance(p, st, 2, n)
+    el = time.perf_counter() - t0
+    return p.cells * n / el, oracle.threads(), n, el
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    p, desc = workload(args.config, args.precision)
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(p, min(per_step, 5.0))
+    vals, cores, nsteps, secs = [], 0, 0, 0.0
+    for _ in range(args.steps):
+        v, cores, n, el = oracle_sample(p, per_step)
+        vals.append(v)
+        nsteps += n
+        secs += el
+    value = p.cells * nsteps / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.config + ": " + desc, "n_max": p.n_max,
+                   "m_points": p.m_points, "precision": "fp64 (oracle)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{nsteps} leap-frog steps of the {p.n_max + 1}x{p.m_points} "
+                                   f"grid from the equilibrium start, in {args.steps} samples"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_1401_6047_gb300 import bte
+
+    p, desc = workload(args.config, args.precision)
+    dt_eff, P, K, Kw = bte.time_grid(p)
+    cells = p.cells
+    elem = 8 if args.precision == "fp64" else 4
+    stream = torch.cuda.Stream(device=dev)
+    solver = bte.Solver(p, stream=stream.cuda_stream, tile_m=args.tile_m, chunk_n=args.chunk_n,
+                        graph_steps=args.graph_steps)
+    graph_len = min(args.graph_steps or 1024, K)
+    launches_per_solve = 3 + K + (K // graph_len) + (1 if K % graph_len else 0) + 1
+
+    # L2 flush buffer (larger than the 129 MB L2), written between timed steps
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one_solve(ev=None):
+        if ev:
+            ev[0].record(stream)
+        solver.reset()
+        if ev:
+            ev[1].record(stream)
+        solver.run()
+        if ev:
+            ev[2].record(stream)
+        o = solver.observables()
+        if ev:
+            ev[3].record(stream)
+        return o
+
+    for _ in range(args.warmup):
+        o = one_solve()
+    if o.status != bte.OK:
+        raise RuntimeError(f"solver status {o.status}")
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    evs = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        o = one_solve(ev)
+        evs.append(ev)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    run_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms, sum(run_ms)], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, run_total = t.tolist()
+    else:
+        run_total = sum(run_ms)
+    value = world * cells * K * args.steps / (total_ms * 1e-3)
+
+    # dominant kernel: the fused step; average duration of one launch over the
+    # timed region (run span / steps; includes inter-launch gaps)
+    avg_launch_s = run_total * 1e-3 / (args.steps * K)
+    alg_bytes = 8 * elem * cells
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / avg_launch_s / 1e9
+    traffic = ncu_traffic(f"{args.config}_{args.precision}")
+
+    result_obs = o
+
+    # end to end through the C ABI with host buffers: create (parameter and
+    # table upload), run, observables (device -> host), destroy
+    e2e = None
+    if not args.no_e2e:
+        pitch = bte.launch_shape(p, args.tile_m, args.chunk_n)["pitch"]
+        h2d = (p.n_max + 1) * elem + 2 * pitch * elem + 2 * (max(P, 1) + 1) * 8
+        d2h = 4 * 8 + 2 * 8 + 4
+        e2e_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            with bte.Solver(p, tile_m=args.tile_m, chunk_n=args.chunk_n,
+                            graph_steps=args.graph_steps) as s2:
+                s2.run()
+                s2.observables()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = t.item()
+        e2e = {"value": world * cells * K * e2e_steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, n, el = oracle_sample(p.replace(precision=0), args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} leap-frog steps of the {p.n_max + 1}x{p.m_points} grid "
+                         f"(FP64 oracle, {el:.1f} s)"}
+
+    solver.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": args.config + ": " + desc, "n_max": p.n_max,
+                       "m_points": p.m_points, "steps_per_solve": K, "dt_eff": dt_eff,
+                       "precision": "fp64" if args.precision == "fp64" else
+                       "fp32 state, fp64 drive/reductions",
+                       "l2": "flushed (256 MB write) before every timed step; the state "
+                             f"({8 * elem * cells / 1e6:.0f} MB ping-pong) stays on chip within a solve "
+                             "where it fits L2",
+                       "parallelism": f"replicas x{world}",
+                       "absorption": result_obs.absorption, "v_dc": result_obs.v_dc_avg,
+                       "norm_max_abs_err": result_obs.norm_max_abs_err},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_kind + " hbm_gbs",
+                         "kernel": "fused_step_kernel",
+                         "alg_bytes_per_launch": alg_bytes,
+                         "avg_launch_us": avg_launch_s * 1e6},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_solve * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "table1"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--tile-m", dest="tile_m", type=int, default=0)
+    ap.add_argument("--chunk-n", dest="chunk_n", type=int, default=0)
+    ap.add_argument("--graph-steps", dest="graph_steps", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,198 @@
+/*
+ * bte.h -- C ABI of the GB300 solver for the two-dimensional, spatially
+ * homogeneous superlattice Boltzmann transport equation
+ *     df/dt + (E + B phi_y) df/dphi_x - B sin(phi_x) df/dphi_y = f0 - f
+ * (Priimak, arXiv:1401.6047, Sec. 2, Eq. boltzmann_final), with the drive
+ * E(t) = E_dc + E_omega cos(omega t) and a constant B.
+ *
+ * f is held as Fourier harmonics a_n(phi_y), b_n(phi_y), n = 0..n_max
+ * (Sec. 2, Eq. f_fourier) on a uniform phi_y grid, and advanced by the
+ * paper's Crank-Nicolson / staggered leap-frog scheme (Sec. 3, Eqs.
+ * a_t_plus_1, b_t_plus_1, leap_frog_1, leap_frog_2).  One time step advances
+ * the whole grid z^t -> z^{t+1} and the fractional grid z^{t+1/2} ->
+ * z^{t+3/2}; both run in one fused CUDA kernel.
+ *
+ * Conventions for every entry point:
+ *   - Functions return a bte_status (0 = BTE_OK).  No exception crosses the
+ *     ABI.  bte_last_error() gives a message for the last failure on the
+ *     calling thread.
+ *   - Pointers to parameters and outputs are HOST pointers owned by the
+ *     caller, unless a comment says "device".
+ *   - A handle owns every device allocation it made; bte_destroy frees them.
+ *   - Work is queued on the handle's CUDA stream; bte_step returns before the
+ *     GPU finishes, bte_observables / bte_trace / bte_get_state synchronise.
+ *   - A handle may be used by one host thread at a time.
+ *
+ * Readings of the paper implemented here (the same ones as the test oracle):
+ *   sigma(0) = 1/2 (Eq. Bolzmann_initial_pdf); b^{t+1} = (g mu' + h nu)/D
+ *   (Eq. b_t_plus_1 with the sign that solves the 2x2 system); stencil
+ *   coefficient B dt/(4 dphi) without alpha; b_0 = 0 (Eq. b_boundary);
+ *   theta at the step start, theta' at its end; start-up half step with
+ *   dt/2; dt adjusted to a whole number of steps per drive period; window
+ *   averages over whole periods; observables from the whole grid.
+ */
+#ifndef BTE_H
+#define BTE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BTE_API __attribute__((visibility("default")))
+#else
+#define BTE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BTE_OK = 0,
+    BTE_EINVAL = -1,    /* invalid argument or parameter                     */
+    BTE_ENOMEM = -2,    /* device allocation failed / workspace too small     */
+    BTE_ECUDA = -3,     /* a CUDA runtime call failed                         */
+    BTE_EUNSTABLE = -4, /* NaN/Inf seen, or |norm - 1| above the threshold    */
+    BTE_ETIMEOUT = -5,  /* a bounded in-kernel wait gave up                   */
+    BTE_ESTATE = -6     /* call not valid in the handle's state               */
+} bte_status;
+
+typedef enum {
+    BTE_FP64 = 0,       /* state, stencil and 2x2 solve in FP64               */
+    BTE_FP32_MIXED = 1  /* FP32 state and stencil in increment form; drive
+                           table, coefficients (rounded once), reductions,
+                           norm and time averages in FP64                     */
+} bte_precision;
+
+/* Problem parameters (dimensionless units of Sec. 2, Eqs. substitutions). */
+typedef struct {
+    double E_dc, E_omega, omega; /* drive E(t) = E_dc + E_omega cos(omega t)   */
+    double B;                    /* magnetic field                             */
+    double mu;                   /* Delta_1 / (2 k_B T), > 0                   */
+    double alpha;                /* m / m_x, > 0 (observables do not depend on it) */
+    double phiy_min, phiy_max;   /* phi_y grid, both ends included             */
+    double dt;                   /* requested step; dt_eff = 2 pi/(omega P),
+                                    P = round(2 pi/(omega dt)) when omega > 0  */
+    double periods;              /* run length in drive periods (omega > 0)   */
+    double t_max;                /* run length in time units (omega == 0)     */
+    double avg_window;           /* averaging window at the end of the run:
+                                    periods (omega > 0) or time (omega == 0)  */
+    int32_t n_max;               /* harmonics n = 0..n_max, >= 1               */
+    int32_t m_points;            /* phi_y points M+1, >= 3                      */
+    int32_t precision;           /* bte_precision                               */
+    int32_t reserved;            /* must be 0                                   */
+} bte_params;
+
+/* Observables (Sec. 2, Eqs. v_dr_generic, norm_in_phi, absorption_def). */
+typedef struct {
+    double t;                /* time of the current whole-grid state          */
+    int64_t step;            /* its step index k (t = k dt_eff)               */
+    double v_dr;             /* pi sqrt(alpha) int b_1 dphi_y at step k        */
+    double norm;             /* 2 pi sqrt(alpha) int a_0 dphi_y at step k      */
+    double v_dc_avg;         /* window mean of v_dr (NaN before the window ends) */
+    double absorption;       /* (2 I_0/I_1) <v_dr cos(omega t)> over the window;
+                                NaN when omega == 0 or the window is not done  */
+    double norm_max_abs_err; /* max over steps 0..k of |norm - 1|              */
+    double dt_eff;           /* time step actually used                        */
+    int64_t steps_total;     /* K, steps of the full run                       */
+    int64_t steps_per_period;/* P (0 when omega == 0)                          */
+    int64_t window_steps;    /* Kw, samples in the averaging window            */
+    int32_t status;          /* bte_status of the run so far                   */
+    int32_t reserved;
+} bte_obs;
+
+/* Optional launch shape of the fused step kernel; 0 fields = automatic. */
+typedef struct {
+    int32_t tile_m;      /* phi_y columns per CTA (multiple of 4, 32..1024)  */
+    int32_t chunk_n;     /* harmonic rows per CTA (>= 4)                     */
+    int32_t graph_steps; /* steps captured per CUDA graph replay (0 = auto)  */
+    int32_t reserved;
+} bte_tuning;
+
+typedef struct bte_handle bte_handle;
+
+/* Device bytes a handle needs for these parameters and launch shape
+ * (state ping-pong, tables, trace, reduction scratch). */
+BTE_API int bte_workspace_size(const bte_params* p, const bte_tuning* tune, size_t* bytes);
+
+/* Creates a solver, initialises f = f0 (a_n = a0_n, b_n = 0; Sec. 2) and
+ * runs the start-up half step (Sec. 3: z^{1/2} = T with dt/2).
+ *   stream : cudaStream_t to queue work on, or NULL for a stream the handle
+ *            creates.
+ * On success *out owns its device memory. */
+BTE_API int bte_create(const bte_params* p, void* stream, bte_handle** out);
+
+/* As bte_create with an explicit launch shape and, when workspace != NULL,
+ * caller-owned DEVICE memory of workspace_bytes >= bte_workspace_size()
+ * bytes (256-byte aligned) used instead of cudaMalloc.  The caller keeps the
+ * workspace alive until bte_destroy. */
+BTE_API int bte_create_ex(const bte_params* p, void* stream, const bte_tuning* tune,
+                  void* workspace, size_t workspace_bytes, bte_handle** out);
+
+/* Queues a return to the initial state of bte_create (f = f0, start-up half
+ * step, step index 0, trace and error word cleared) without reallocating. */
+BTE_API int bte_reset(bte_handle* h);
+
+/* Queues nsteps leap-frog steps (Eqs. leap_frog_1, leap_frog_2) after the
+ * current one.  BTE_ESTATE if that would pass steps_total. */
+BTE_API int bte_step(bte_handle* h, int64_t nsteps);
+
+/* Queues the remaining steps of the run (to steps_total). */
+BTE_API int bte_run(bte_handle* h);
+
+/* Waits for queued work and fills *out; the window results are final once
+ * step == steps_total.  Returns the run status (BTE_EUNSTABLE when a NaN,
+ * an Inf or |norm - 1| > 0.05 was seen; BTE_ETIMEOUT after a bounded wait in
+ * a kernel gave up). */
+BTE_API int bte_observables(bte_handle* h, bte_obs* out);
+
+/* Copies whole-grid samples k0..k0+count-1 of v_dr and norm (HOST arrays,
+ * either may be NULL).  Samples beyond the current step are BTE_EINVAL. */
+BTE_API int bte_trace(bte_handle* h, int64_t k0, int64_t count, double* v, double* norm);
+
+/* State of one grid (0 = whole grid at step k, 1 = fractional grid at
+ * k + 1/2) as HOST FP64 arrays a[n_max+1][m_points], b[n_max+1][m_points]
+ * (row n, column m, row-major).  FP32 state is widened exactly. */
+BTE_API int bte_get_state(bte_handle* h, int grid, double* a, double* b);
+
+/* Overwrites one grid from HOST FP64 arrays laid out as in bte_get_state
+ * (FP32 state rounds to nearest).  b[0][*] must be 0. */
+BTE_API int bte_set_state(bte_handle* h, int grid, const double* a, const double* b);
+
+/* Sets the current step index to k (0 <= k <= steps_total) and restores the
+ * whole-grid samples 0..k (HOST arrays of length k+1) that the window
+ * averages and norm error are computed from.  Used with bte_set_state to
+ * resume from a checkpoint. */
+BTE_API int bte_set_step(bte_handle* h, int64_t k, const double* v, const double* norm);
+
+/* Frees the handle and everything it allocated.  NULL is ignored. */
+BTE_API void bte_destroy(bte_handle* h);
+
+/* Message of the last failing call on this thread ("" if none). */
+BTE_API const char* bte_last_error(void);
+
+/* I_n(mu)/I_0(mu), n = 0..nmax, into HOST array r (Miller's backward
+ * recurrence); the library's own equilibrium coefficients (Sec. 2,
+ * Eq. Bolzmann_initial_pdf) come from it.  Host-only, needs no GPU. */
+BTE_API int bte_bessel_ratio(double mu, int32_t nmax, double* r);
+
+/* Time grid of a parameter set: dt_eff, steps per period P, total steps K,
+ * window samples Kw (any pointer may be NULL).  Host-only. */
+BTE_API int bte_time_grid(const bte_params* p, double* dt_eff, int64_t* P, int64_t* K,
+                  int64_t* Kw);
+
+/* Launch shape of the fused step kernel and row pitch (elements) of the
+ * device arrays that bte_create_ex would choose for p and tune (any output
+ * pointer may be NULL).  Host-only. */
+BTE_API int bte_launch_shape(const bte_params* p, const bte_tuning* tune, int32_t* tile_m,
+                             int32_t* chunk_n, int32_t* pitch, int32_t* grid_x,
+                             int32_t* grid_y);
+
+/* Library version string. */
+BTE_API const char* bte_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BTE_H */

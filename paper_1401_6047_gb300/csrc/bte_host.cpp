@@ -1,0 +1,715 @@
+/*
+ * bte_host.cpp -- host side of the C ABI declared in include/bte.h.
+ *
+ * Responsibilities: parameter validation, the time grid, the equilibrium
+ * coefficients (Miller's backward recurrence for I_n(mu)/I_0(mu)), the drive
+ * table, the device layout, kernel launch shapes, CUDA-graph capture of runs
+ * of steps, state and trace transfers.  All arithmetic of a time step runs
+ * in the kernels of bte_kernels.cu.
+ */
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/bte.h"
+#include "bte_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(BTE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
+    } while (0)
+
+const double kTwoPi = 6.283185307179586476925286766559;
+const double kPi = 3.14159265358979323846264338328;
+
+struct TimeGrid {
+    double dt_eff;
+    long long P, K, Kw;
+};
+
+int validate(const bte_params* p) {
+    if (!p) return fail(BTE_EINVAL, "params is NULL");
+    const double v[] = {p->E_dc, p->E_omega, p->omega, p->B, p->mu, p->alpha,
+                        p->phiy_min, p->phiy_max, p->dt, p->periods, p->t_max, p->avg_window};
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(BTE_EINVAL, "non-finite parameter");
+    if (p->n_max < 1) return fail(BTE_EINVAL, "n_max must be >= 1");
+    if (p->m_points < 3) return fail(BTE_EINVAL, "m_points must be >= 3");
+    if (p->mu <= 0) return fail(BTE_EINVAL, "mu must be > 0");
+    if (p->alpha <= 0) return fail(BTE_EINVAL, "alpha must be > 0");
+    if (p->dt <= 0) return fail(BTE_EINVAL, "dt must be > 0");
+    if (p->omega < 0) return fail(BTE_EINVAL, "omega must be >= 0");
+    if (!(p->phiy_max > p->phiy_min)) return fail(BTE_EINVAL, "phiy_max must exceed phiy_min");
+    if (p->avg_window < 0) return fail(BTE_EINVAL, "avg_window must be >= 0");
+    if (p->precision != BTE_FP64 && p->precision != BTE_FP32_MIXED)
+        return fail(BTE_EINVAL, "unknown precision %d", p->precision);
+    if (p->reserved != 0) return fail(BTE_EINVAL, "reserved field must be 0");
+    if (p->omega > 0) {
+        if (p->periods <= 0) return fail(BTE_EINVAL, "periods must be > 0 when omega > 0");
+        if (p->avg_window > p->periods) return fail(BTE_EINVAL, "avg_window exceeds the run");
+    } else {
+        if (p->t_max <= 0) return fail(BTE_EINVAL, "t_max must be > 0 when omega == 0");
+        if (p->avg_window > p->t_max) return fail(BTE_EINVAL, "avg_window exceeds the run");
+    }
+    if ((long long)(p->n_max + 1) * (long long)p->m_points > (1ll << 31))
+        return fail(BTE_EINVAL, "grid too large");
+    return BTE_OK;
+}
+
+int time_grid(const bte_params* p, TimeGrid& g) {
+    if (p->omega > 0) {
+        const double Pd = std::nearbyint(kTwoPi / (p->omega * p->dt));
+        if (!(Pd >= 1.0) || Pd > 1e9) return fail(BTE_EINVAL, "steps per period out of range");
+        g.P = (long long)Pd;
+        g.dt_eff = kTwoPi / (p->omega * (double)g.P);
+        g.K = std::llround(p->periods * (double)g.P);
+        g.Kw = std::llround(p->avg_window * (double)g.P);
+    } else {
+        g.P = 0;
+        g.dt_eff = p->dt;
+        g.K = std::llround(p->t_max / p->dt);
+        g.Kw = std::llround(p->avg_window / p->dt);
+    }
+    if (g.K < 1 || g.K > (1ll << 40)) return fail(BTE_EINVAL, "run length out of range");
+    if (g.Kw > g.K) g.Kw = g.K;
+    if (g.Kw < 1) g.Kw = 1;
+    return BTE_OK;
+}
+
+/* Miller's backward recurrence (J.C.P. Miller, 1952) for the minimal
+ * solution of I_{n-1}(x) = (2n/x) I_n(x) + I_{n+1}(x): start far above the
+ * highest order needed with (I_{s+1}, I_s) = (0, 1), recur downward and
+ * divide by the I_0 obtained.  Values are rescaled when they grow large;
+ * orders above nmax are not kept. */
+void miller_ratio(double x, int nmax, double* r) {
+    const int s = nmax + 32 + (int)std::ceil(x) + (int)std::ceil(8.0 * std::sqrt(x + nmax + 16.0));
+    std::vector<double> I(nmax + 1, 0.0);
+    double ip1 = 0.0, in = 1.0; /* I_{n+1}, I_n at n = s */
+    for (int n = s; n >= 1; --n) {
+        double im1 = (2.0 * n / x) * in + ip1;
+        ip1 = in;
+        in = im1;
+        if (n - 1 <= nmax) I[n - 1] = im1;
+        if (n <= nmax) I[n] = ip1;
+        if (std::fabs(in) > 1e250) {
+            in *= 1e-250;
+            ip1 *= 1e-250;
+            for (int q = std::max(n - 1, 0); q <= nmax; ++q) I[q] *= 1e-250;
+        }
+    }
+    for (int n = 0; n <= nmax; ++n) r[n] = I[n] / I[0];
+}
+
+int pick_tile(const bte_params* p, const bte_tuning* t, int& tile_m, int& chunk_n) {
+    const int M1 = p->m_points, N1 = p->n_max + 1;
+    tile_m = (t && t->tile_m) ? t->tile_m : 0;
+    chunk_n = (t && t->chunk_n) ? t->chunk_n : 0;
+    if (tile_m) {
+        if (tile_m % 4 || tile_m < 32 || tile_m > 1024)
+            return fail(BTE_EINVAL, "tile_m must be a multiple of 4 in 32..1024");
+    } else {
+        /* fewest wasted columns, preferring wider tiles on ties */
+        const int cand[] = {512, 384, 320, 256, 192, 128};
+        int best = 256;
+        double best_cost = 1e30;
+        for (int c : cand) {
+            const int ntx = (M1 + c - 1) / c;
+            const double waste = (double)(ntx * c - M1) / M1;
+            const double halo = 8.0 / c; /* re-read halo columns */
+            const double cost = waste + halo;
+            if (cost < best_cost - 1e-9) {
+                best_cost = cost;
+                best = c;
+            }
+        }
+        tile_m = best;
+        if (M1 < tile_m) tile_m = std::max(32, (M1 + 3) / 4 * 4);
+    }
+    if (chunk_n) {
+        if (chunk_n < 4) return fail(BTE_EINVAL, "chunk_n must be >= 4");
+    } else {
+        const int ntx = (M1 + tile_m - 1) / tile_m;
+        const int want = 4 * 152; /* enough CTAs for a few per SM */
+        chunk_n = 64;
+        while (chunk_n > 8 && (long long)ntx * ((N1 + chunk_n - 1) / chunk_n) < want) chunk_n /= 2;
+    }
+    return BTE_OK;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+    int G, pitch, tile_m, chunk_n, ntx, nty;
+    size_t elem;
+    size_t off_state[8];
+    size_t off_row_a0, off_col_g, off_col_bphi, off_ew, off_ef, off_tv, off_tn, off_part,
+        off_ticket, off_err, off_base, off_fin, total;
+};
+
+int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L) {
+    int rc = pick_tile(p, t, L.tile_m, L.chunk_n);
+    if (rc) return rc;
+    L.elem = p->precision == BTE_FP64 ? 8 : 4;
+    L.G = (int)(16 / L.elem);
+    const size_t smem = L.elem == 8 ? bte::step_smem_bytes<double>(L.tile_m)
+                                    : bte::step_smem_bytes<float>(L.tile_m);
+    if (smem > 227 * 1024)
+        return fail(BTE_EINVAL, "tile_m %d needs %zu bytes of shared memory", L.tile_m, smem);
+    const int M1 = p->m_points, N1 = p->n_max + 1;
+    L.ntx = (M1 + L.tile_m - 1) / L.tile_m;
+    L.nty = (N1 + L.chunk_n - 1) / L.chunk_n;
+    /* the last tile reads up to column G + ntx*tile_m + G - 1 */
+    L.pitch = (int)align_up((size_t)(L.ntx * L.tile_m + 2 * L.G), 32);
+    size_t o = 0;
+    const size_t arr = align_up((size_t)N1 * L.pitch * L.elem, 256);
+    for (int q = 0; q < 8; ++q) {
+        L.off_state[q] = o;
+        o += arr;
+    }
+    L.off_row_a0 = o;
+    o += align_up((size_t)N1 * L.elem, 256);
+    L.off_col_g = o;
+    o += align_up((size_t)L.pitch * L.elem, 256);
+    L.off_col_bphi = o;
+    o += align_up((size_t)L.pitch * L.elem, 256);
+    const long long Pt = tg.P > 0 ? tg.P : 1;
+    L.off_ew = o;
+    o += align_up((size_t)(Pt + 1) * 8, 256);
+    L.off_ef = o;
+    o += align_up((size_t)(Pt + 1) * 8, 256);
+    L.off_tv = o;
+    o += align_up((size_t)(tg.K + 1) * 8, 256);
+    L.off_tn = o;
+    o += align_up((size_t)(tg.K + 1) * 8, 256);
+    L.off_part = o;
+    o += align_up((size_t)2 * L.ntx * 8, 256);
+    L.off_ticket = o;
+    o += 256;
+    L.off_err = o;
+    o += 256;
+    L.off_base = o;
+    o += 256;
+    L.off_fin = o;
+    o += 256;
+    L.total = o;
+    return BTE_OK;
+}
+
+}  // namespace
+
+struct bte_handle {
+    bte_params p;
+    TimeGrid tg;
+    Layout L;
+    bool fp64;
+    bool own_mem;
+    bool own_stream;
+    unsigned char* mem;
+    cudaStream_t stream;
+    cudaStream_t cap_stream;
+    long long k;   /* steps queued so far */
+    long long base_host;
+    int graph_len;
+    cudaGraphExec_t graph;
+    double r1;     /* I_1/I_0 */
+    double dphi;
+    template <typename T>
+    T* ptr(size_t off) const {
+        return reinterpret_cast<T*>(mem + off);
+    }
+};
+
+namespace {
+
+template <typename T>
+bte::StepArgs<T> step_args(const bte_handle* h) {
+    bte::StepArgs<T> a;
+    const Layout& L = h->L;
+    for (int s = 0; s < 2; ++s) {
+        a.a_w[s] = h->ptr<T>(L.off_state[4 * s + 0]);
+        a.b_w[s] = h->ptr<T>(L.off_state[4 * s + 1]);
+        a.a_f[s] = h->ptr<T>(L.off_state[4 * s + 2]);
+        a.b_f[s] = h->ptr<T>(L.off_state[4 * s + 3]);
+    }
+    a.row_a0 = h->ptr<T>(L.off_row_a0);
+    a.col_g = h->ptr<T>(L.off_col_g);
+    a.col_bphi = h->ptr<T>(L.off_col_bphi);
+    a.e_whole = h->ptr<double>(L.off_ew);
+    a.e_frac = h->ptr<double>(L.off_ef);
+    a.base = h->ptr<long long>(L.off_base);
+    a.trace_v = h->ptr<double>(L.off_tv);
+    a.trace_n = h->ptr<double>(L.off_tn);
+    a.part = h->ptr<double>(L.off_part);
+    a.ticket = h->ptr<unsigned>(L.off_ticket);
+    a.err = h->ptr<int>(L.off_err);
+    a.N = h->p.n_max;
+    a.M = h->p.m_points - 1;
+    a.pitch = L.pitch;
+    a.P = h->tg.P > 0 ? (int)h->tg.P : 1;
+    a.tile_m = L.tile_m;
+    a.chunk_n = L.chunk_n;
+    a.ntx = L.ntx;
+    a.nty = L.nty;
+    const double dt = h->tg.dt_eff;
+    a.h = (T)dt;
+    a.hh = (T)(0.5 * dt);
+    a.nu = (T)(1.0 + 0.5 * dt);
+    a.xi = (T)(1.0 - 0.5 * dt);
+    a.c = (T)(h->p.B * dt / (4.0 * h->dphi));
+    const double sq = std::sqrt(h->p.alpha);
+    a.vscale = kPi * sq * h->dphi;
+    a.nscale = 2.0 * kPi * sq * h->dphi;
+    return a;
+}
+
+template <typename T>
+int upload_tables(bte_handle* h) {
+    const bte_params& p = h->p;
+    const Layout& L = h->L;
+    const int N1 = p.n_max + 1, M1 = p.m_points;
+    std::vector<double> r(N1);
+    miller_ratio(p.mu, p.n_max, r.data());
+    h->r1 = r[1];
+    std::vector<T> row(N1), colg(L.pitch, (T)0), colb(L.pitch, (T)0);
+    for (int n = 0; n < N1; ++n) row[n] = (T)((n == 0 ? 0.5 : 1.0) * r[n] / kPi);
+    const double pref = std::sqrt(p.mu / (2.0 * kPi * p.alpha));
+    for (int m = 0; m < M1; ++m) {
+        const double phi = p.phiy_min + m * h->dphi;
+        colg[L.G + m] = (T)(pref * std::exp(-0.5 * p.mu * phi * phi));
+        colb[L.G + m] = (T)(p.B * phi);
+    }
+    const long long Pt = h->tg.P > 0 ? h->tg.P : 1;
+    std::vector<double> ew(Pt + 1), ef(Pt + 1);
+    for (long long q = 0; q <= Pt; ++q) {
+        if (h->tg.P > 0) {
+            ew[q] = p.E_dc + p.E_omega * std::cos(kTwoPi * (double)q / (double)Pt);
+            ef[q] = p.E_dc + p.E_omega * std::cos(kTwoPi * ((double)q + 0.5) / (double)Pt);
+        } else {
+            ew[q] = ef[q] = p.E_dc + p.E_omega;
+        }
+    }
+    CU(cudaMemcpyAsync(h->ptr<T>(L.off_row_a0), row.data(), N1 * sizeof(T), cudaMemcpyHostToDevice,
+                       h->stream));
+    CU(cudaMemcpyAsync(h->ptr<T>(L.off_col_g), colg.data(), L.pitch * sizeof(T),
+                       cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(h->ptr<T>(L.off_col_bphi), colb.data(), L.pitch * sizeof(T),
+                       cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(h->ptr<double>(L.off_ew), ew.data(), (Pt + 1) * 8, cudaMemcpyHostToDevice,
+                       h->stream));
+    CU(cudaMemcpyAsync(h->ptr<double>(L.off_ef), ef.data(), (Pt + 1) * 8, cudaMemcpyHostToDevice,
+                       h->stream));
+    CU(cudaStreamSynchronize(h->stream)); /* host vectors go out of scope */
+    return BTE_OK;
+}
+
+/* f = f0 on the whole grid, then z^{1/2} = T_{dt/2}(z^0; S(z^0)) (Sec. 3).
+ * `full` clears every buffer (creation); otherwise only the counters and the
+ * error word are cleared, since the kernels rewrite every interior cell and
+ * never write ghost cells. */
+template <typename T>
+int initialise(bte_handle* h, bool full, bool sync) {
+    const Layout& L = h->L;
+    const bte_params& p = h->p;
+    if (full) {
+        CU(cudaMemsetAsync(h->mem, 0, L.off_row_a0, h->stream));
+        CU(cudaMemsetAsync(h->mem + L.off_tv, 0, L.off_fin + 256 - L.off_tv, h->stream));
+    } else {
+        CU(cudaMemsetAsync(h->mem + L.off_ticket, 0, L.off_fin - L.off_ticket, h->stream));
+    }
+    T* aw = h->ptr<T>(L.off_state[0]);
+    T* bw = h->ptr<T>(L.off_state[1]);
+    int rc = bte::launch_init<T>(aw, bw, h->ptr<T>(L.off_row_a0), h->ptr<T>(L.off_col_g), p.n_max,
+                                 p.m_points - 1, L.pitch, h->stream);
+    if (rc) return fail(BTE_ECUDA, "init kernel: %s", cudaGetErrorString((cudaError_t)rc));
+    bte::ApplyArgs<T> a;
+    a.a = aw;
+    a.b = bw;
+    a.as = aw;
+    a.bs = bw;
+    a.an = h->ptr<T>(L.off_state[2]);
+    a.bn = h->ptr<T>(L.off_state[3]);
+    a.row_a0 = h->ptr<T>(L.off_row_a0);
+    a.col_g = h->ptr<T>(L.off_col_g);
+    a.col_bphi = h->ptr<T>(L.off_col_bphi);
+    a.N = p.n_max;
+    a.M = p.m_points - 1;
+    a.pitch = L.pitch;
+    const double hs = 0.5 * h->tg.dt_eff;
+    a.E_start = p.E_dc + p.E_omega;
+    a.E_end = p.E_dc + p.E_omega * std::cos(p.omega * hs);
+    a.h = (T)hs;
+    a.hh = (T)(0.5 * hs);
+    a.nu = (T)(1.0 + 0.5 * hs);
+    a.xi = (T)(1.0 - 0.5 * hs);
+    a.c = (T)(p.B * hs / (4.0 * h->dphi));
+    rc = bte::launch_apply<T>(a, h->stream);
+    if (rc) return fail(BTE_ECUDA, "start-up kernel: %s", cudaGetErrorString((cudaError_t)rc));
+    const bte::StepArgs<T> sa = step_args<T>(h);
+    rc = bte::launch_observe<T>(aw, bw, p.m_points - 1, L.pitch, sa.vscale, sa.nscale, sa.trace_v,
+                                sa.trace_n, 0, h->stream);
+    if (rc) return fail(BTE_ECUDA, "observe kernel: %s", cudaGetErrorString((cudaError_t)rc));
+    h->k = 0;
+    h->base_host = 0;
+    if (sync) CU(cudaStreamSynchronize(h->stream));
+    return BTE_OK;
+}
+
+template <typename T>
+int enqueue_steps(bte_handle* h, long long n) {
+    const bte::StepArgs<T> a = step_args<T>(h);
+    long long* base = h->ptr<long long>(h->L.off_base);
+    if (h->graph_len > 1 && n >= h->graph_len && !h->graph) {
+        /* capture graph_len fused steps plus the counter update once */
+        cudaGraph_t g = nullptr;
+        CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = 0;
+        for (int i = 0; i < h->graph_len && !rc; ++i) rc = bte::launch_step<T>(a, i, h->cap_stream);
+        if (!rc) rc = bte::launch_advance_base(base, h->graph_len, h->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+        if (rc || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(BTE_ECUDA, "graph capture failed: %s",
+                        cudaGetErrorString(e != cudaSuccess ? e : (cudaError_t)rc));
+        }
+        e = cudaGraphInstantiate(&h->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            h->graph = nullptr;
+            return fail(BTE_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+        }
+    }
+    while (h->graph && n >= h->graph_len) {
+        CU(cudaGraphLaunch(h->graph, h->stream));
+        n -= h->graph_len;
+        h->k += h->graph_len;
+    }
+    if (n > 0) {
+        for (long long i = 0; i < n; ++i) {
+            int rc = bte::launch_step<T>(a, (int)i, h->stream);
+            if (rc) return fail(BTE_ECUDA, "step kernel: %s", cudaGetErrorString((cudaError_t)rc));
+        }
+        int rc = bte::launch_advance_base(base, n, h->stream);
+        if (rc) return fail(BTE_ECUDA, "counter kernel: %s", cudaGetErrorString((cudaError_t)rc));
+        h->k += n;
+    }
+    return BTE_OK;
+}
+
+template <typename T>
+int get_grid(bte_handle* h, int grid, double* a, double* b) {
+    const Layout& L = h->L;
+    const int set = (int)(h->k & 1);
+    const int N1 = h->p.n_max + 1, M1 = h->p.m_points;
+    const T* da = h->ptr<T>(L.off_state[4 * set + 2 * grid + 0]);
+    const T* db = h->ptr<T>(L.off_state[4 * set + 2 * grid + 1]);
+    std::vector<T> buf((size_t)N1 * M1);
+    for (int which = 0; which < 2; ++which) {
+        const T* src = which ? db : da;
+        double* dst = which ? b : a;
+        if (!dst) continue;
+        CU(cudaMemcpy2DAsync(buf.data(), M1 * sizeof(T), src + L.G, L.pitch * sizeof(T),
+                             M1 * sizeof(T), N1, cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        for (size_t q = 0; q < buf.size(); ++q) dst[q] = (double)buf[q];
+    }
+    return BTE_OK;
+}
+
+template <typename T>
+int set_grid(bte_handle* h, int grid, const double* a, const double* b) {
+    const Layout& L = h->L;
+    const int set = (int)(h->k & 1);
+    const int N1 = h->p.n_max + 1, M1 = h->p.m_points;
+    for (int m = 0; m < M1; ++m)
+        if (b[m] != 0.0) return fail(BTE_EINVAL, "b[0][*] must be 0 (Eq. b_boundary)");
+    std::vector<T> buf((size_t)N1 * M1);
+    for (int which = 0; which < 2; ++which) {
+        const double* src = which ? b : a;
+        T* dst = h->ptr<T>(L.off_state[4 * set + 2 * grid + which]);
+        for (size_t q = 0; q < buf.size(); ++q) buf[q] = (T)src[q];
+        CU(cudaMemcpy2DAsync(dst + L.G, L.pitch * sizeof(T), buf.data(), M1 * sizeof(T),
+                             M1 * sizeof(T), N1, cudaMemcpyHostToDevice, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+    }
+    return BTE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bte_last_error(void) { return g_err.c_str(); }
+
+const char* bte_version(void) { return "bte-gb300 0.1 (sm_103a)"; }
+
+int bte_bessel_ratio(double mu, int32_t nmax, double* r) {
+    if (!(mu > 0) || !std::isfinite(mu) || nmax < 0 || !r)
+        return fail(BTE_EINVAL, "bte_bessel_ratio: bad argument");
+    miller_ratio(mu, nmax, r);
+    return BTE_OK;
+}
+
+int bte_time_grid(const bte_params* p, double* dt_eff, int64_t* P, int64_t* K, int64_t* Kw) {
+    int rc = validate(p);
+    if (rc) return rc;
+    TimeGrid g;
+    rc = time_grid(p, g);
+    if (rc) return rc;
+    if (dt_eff) *dt_eff = g.dt_eff;
+    if (P) *P = g.P;
+    if (K) *K = g.K;
+    if (Kw) *Kw = g.Kw;
+    return BTE_OK;
+}
+
+int bte_workspace_size(const bte_params* p, const bte_tuning* tune, size_t* bytes) {
+    int rc = validate(p);
+    if (rc) return rc;
+    if (!bytes) return fail(BTE_EINVAL, "bytes is NULL");
+    TimeGrid g;
+    rc = time_grid(p, g);
+    if (rc) return rc;
+    Layout L;
+    rc = plan(p, tune, g, L);
+    if (rc) return rc;
+    *bytes = L.total;
+    return BTE_OK;
+}
+
+int bte_launch_shape(const bte_params* p, const bte_tuning* tune, int32_t* tile_m,
+                     int32_t* chunk_n, int32_t* pitch, int32_t* grid_x, int32_t* grid_y) {
+    int rc = validate(p);
+    if (rc) return rc;
+    TimeGrid g;
+    rc = time_grid(p, g);
+    if (rc) return rc;
+    Layout L;
+    rc = plan(p, tune, g, L);
+    if (rc) return rc;
+    if (tile_m) *tile_m = L.tile_m;
+    if (chunk_n) *chunk_n = L.chunk_n;
+    if (pitch) *pitch = L.pitch;
+    if (grid_x) *grid_x = L.ntx;
+    if (grid_y) *grid_y = L.nty;
+    return BTE_OK;
+}
+
+int bte_create_ex(const bte_params* p, void* stream, const bte_tuning* tune, void* workspace,
+                  size_t workspace_bytes, bte_handle** out) {
+    if (!out) return fail(BTE_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc) return rc;
+    bte_handle* h = new (std::nothrow) bte_handle();
+    if (!h) return fail(BTE_ENOMEM, "host allocation failed");
+    h->p = *p;
+    h->fp64 = p->precision == BTE_FP64;
+    h->dphi = (p->phiy_max - p->phiy_min) / (p->m_points - 1);
+    rc = time_grid(p, h->tg);
+    if (!rc) rc = plan(p, tune, h->tg, h->L);
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    h->graph_len = (tune && tune->graph_steps > 0) ? tune->graph_steps : 1024;
+    if (h->graph_len > h->tg.K) h->graph_len = (int)h->tg.K;
+    auto bail = [&](int code) {
+        bte_destroy(h);
+        return code;
+    };
+    if (stream) {
+        h->stream = (cudaStream_t)stream;
+        h->own_stream = false;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete h;
+            return fail(BTE_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        }
+        h->own_stream = true;
+    }
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(fail(BTE_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
+    }
+    if (workspace) {
+        if (workspace_bytes < h->L.total)
+            return bail(fail(BTE_ENOMEM, "workspace of %zu bytes, %zu needed", workspace_bytes,
+                             h->L.total));
+        if ((uintptr_t)workspace % 256)
+            return bail(fail(BTE_EINVAL, "workspace must be 256-byte aligned"));
+        h->mem = (unsigned char*)workspace;
+        h->own_mem = false;
+    } else {
+        cudaError_t e = cudaMalloc(&h->mem, h->L.total);
+        if (e != cudaSuccess) {
+            h->mem = nullptr;
+            cudaGetLastError();
+            return bail(fail(BTE_ENOMEM, "cudaMalloc(%zu): %s", h->L.total, cudaGetErrorString(e)));
+        }
+        h->own_mem = true;
+    }
+    rc = h->fp64 ? bte::step_kernel_configure<double>(h->L.tile_m)
+                 : bte::step_kernel_configure<float>(h->L.tile_m);
+    if (rc) return bail(fail(BTE_ECUDA, "kernel configure: %s", cudaGetErrorString((cudaError_t)rc)));
+    rc = h->fp64 ? upload_tables<double>(h) : upload_tables<float>(h);
+    if (rc) return bail(rc);
+    rc = h->fp64 ? initialise<double>(h, true, true) : initialise<float>(h, true, true);
+    if (rc) return bail(rc);
+    *out = h;
+    return BTE_OK;
+}
+
+int bte_create(const bte_params* p, void* stream, bte_handle** out) {
+    return bte_create_ex(p, stream, nullptr, nullptr, 0, out);
+}
+
+int bte_reset(bte_handle* h) {
+    if (!h) return fail(BTE_EINVAL, "handle is NULL");
+    return h->fp64 ? initialise<double>(h, false, false) : initialise<float>(h, false, false);
+}
+
+int bte_step(bte_handle* h, int64_t nsteps) {
+    if (!h) return fail(BTE_EINVAL, "handle is NULL");
+    if (nsteps < 0) return fail(BTE_EINVAL, "nsteps < 0");
+    if (h->k + nsteps > h->tg.K)
+        return fail(BTE_ESTATE, "step %lld + %lld passes the end of the run (%lld)", h->k,
+                    (long long)nsteps, h->tg.K);
+    return h->fp64 ? enqueue_steps<double>(h, nsteps) : enqueue_steps<float>(h, nsteps);
+}
+
+int bte_run(bte_handle* h) {
+    if (!h) return fail(BTE_EINVAL, "handle is NULL");
+    return bte_step(h, h->tg.K - h->k);
+}
+
+int bte_observables(bte_handle* h, bte_obs* out) {
+    if (!h || !out) return fail(BTE_EINVAL, "NULL argument");
+    const Layout& L = h->L;
+    bte::FinalArgs f;
+    f.trace_v = h->ptr<double>(L.off_tv);
+    f.trace_n = h->ptr<double>(L.off_tn);
+    f.k = h->k;
+    f.K = h->tg.K;
+    f.Kw = h->tg.Kw;
+    f.P = h->tg.P;
+    f.omega = h->p.omega;
+    f.dt_eff = h->tg.dt_eff;
+    f.inv_r1 = 1.0 / h->r1;
+    f.out = h->ptr<double>(L.off_fin);
+    int rc = bte::launch_finalize(f, h->stream);
+    if (rc) return fail(BTE_ECUDA, "finalize kernel: %s", cudaGetErrorString((cudaError_t)rc));
+    double fin[4], vn[2];
+    int err = 0;
+    CU(cudaMemcpyAsync(fin, f.out, sizeof fin, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(&vn[0], f.trace_v + h->k, 8, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(&vn[1], f.trace_n + h->k, 8, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(&err, h->ptr<int>(L.off_err), sizeof err, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    const bool done = h->k == h->tg.K;
+    out->t = h->k * h->tg.dt_eff;
+    out->step = h->k;
+    out->v_dr = vn[0];
+    out->norm = vn[1];
+    out->v_dc_avg = done ? fin[1] : NAN;
+    out->absorption = (done && h->p.omega > 0) ? fin[0] : NAN;
+    out->norm_max_abs_err = fin[2];
+    out->dt_eff = h->tg.dt_eff;
+    out->steps_total = h->tg.K;
+    out->steps_per_period = h->tg.P;
+    out->window_steps = h->tg.Kw;
+    int st = BTE_OK;
+    if (err) st = BTE_ETIMEOUT;
+    else if (fin[3] != 0.0 || !(fin[2] <= 0.05)) st = BTE_EUNSTABLE;
+    out->status = st;
+    out->reserved = 0;
+    if (st == BTE_ETIMEOUT) return fail(st, "a bounded wait in the step kernel gave up");
+    if (st == BTE_EUNSTABLE)
+        return fail(st, "unstable run: |norm-1| reached %g%s", fin[2],
+                    fin[3] != 0.0 ? " (non-finite values)" : "");
+    return BTE_OK;
+}
+
+int bte_trace(bte_handle* h, int64_t k0, int64_t count, double* v, double* norm) {
+    if (!h) return fail(BTE_EINVAL, "handle is NULL");
+    if (k0 < 0 || count < 0 || k0 + count > h->k + 1)
+        return fail(BTE_EINVAL, "trace range [%lld, %lld) outside 0..%lld", (long long)k0,
+                    (long long)(k0 + count), h->k);
+    if (count == 0) return BTE_OK;
+    if (v)
+        CU(cudaMemcpyAsync(v, h->ptr<double>(h->L.off_tv) + k0, count * 8, cudaMemcpyDeviceToHost,
+                           h->stream));
+    if (norm)
+        CU(cudaMemcpyAsync(norm, h->ptr<double>(h->L.off_tn) + k0, count * 8,
+                           cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return BTE_OK;
+}
+
+int bte_get_state(bte_handle* h, int grid, double* a, double* b) {
+    if (!h || (grid != 0 && grid != 1)) return fail(BTE_EINVAL, "bad handle or grid");
+    return h->fp64 ? get_grid<double>(h, grid, a, b) : get_grid<float>(h, grid, a, b);
+}
+
+int bte_set_state(bte_handle* h, int grid, const double* a, const double* b) {
+    if (!h || (grid != 0 && grid != 1) || !a || !b) return fail(BTE_EINVAL, "bad argument");
+    return h->fp64 ? set_grid<double>(h, grid, a, b) : set_grid<float>(h, grid, a, b);
+}
+
+int bte_set_step(bte_handle* h, int64_t k, const double* v, const double* norm) {
+    if (!h || !v || !norm) return fail(BTE_EINVAL, "bad argument");
+    if (k < 0 || k > h->tg.K) return fail(BTE_EINVAL, "step %lld outside 0..%lld", (long long)k, h->tg.K);
+    /* the state of step k must sit in ping-pong set (k & 1): move it if the
+     * parity changes */
+    if ((k & 1) != (h->k & 1)) {
+        const Layout& L = h->L;
+        const int from = (int)(h->k & 1), to = from ^ 1;
+        for (int q = 0; q < 4; ++q)
+            CU(cudaMemcpyAsync(h->mem + L.off_state[4 * to + q], h->mem + L.off_state[4 * from + q],
+                               L.off_state[1] - L.off_state[0], cudaMemcpyDeviceToDevice, h->stream));
+    }
+    h->base_host = k;
+    CU(cudaMemcpyAsync(h->ptr<long long>(h->L.off_base), &h->base_host, 8, cudaMemcpyHostToDevice,
+                       h->stream));
+    CU(cudaMemcpyAsync(h->ptr<double>(h->L.off_tv), v, (k + 1) * 8, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(h->ptr<double>(h->L.off_tn), norm, (k + 1) * 8, cudaMemcpyHostToDevice,
+                       h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    h->k = k;
+    return BTE_OK;
+}
+
+void bte_destroy(bte_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->own_mem && h->mem) cudaFree(h->mem);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+}  /* extern "C" */

@@ -1,0 +1,87 @@
+/*
+ * bte_internal.h -- structures shared by the library's host code and its
+ * CUDA kernels.  Not part of the public ABI.
+ *
+ * Device layout of one grid array (a or b, whole or fractional grid):
+ *   rows n = 0..N (N = n_max), row pitch `pitch` elements, column m of the
+ *   phi_y grid at physical index G + m with G = 16 / sizeof(T) zero ghost
+ *   columns on the left; columns G+M+1 .. pitch-1 are zero ghosts too.
+ *   Ghost columns are written once (zero) and never again, so the stencil
+ *   at m = 0 and m = M reads the boundary value 0 of Eqs. a_boundary and
+ *   b_boundary without a branch.  Rows outside 0..N are never stored; the
+ *   kernels substitute 0 for them.
+ */
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+namespace bte {
+
+/* value stored in the device error word when a bounded wait gives up */
+constexpr int kErrTimeout = 1;
+
+/* Arguments of the fused step kernel (one leap-frog step). */
+template <typename T>
+struct StepArgs {
+    T* a_w[2];            /* ping-pong sets: set (k & 1) holds step k           */
+    T* b_w[2];
+    T* a_f[2];
+    T* b_f[2];
+    const T* row_a0;      /* [N+1]   sigma_n I_n/I_0 / pi                        */
+    const T* col_g;       /* [pitch] sqrt(mu/(2 pi alpha)) exp(-mu phi^2/2), 0 in ghosts */
+    const T* col_bphi;    /* [pitch] B phi_y(m), 0 in ghosts                    */
+    const double* e_whole;/* [P+1]   E(i dt_eff)                                 */
+    const double* e_frac; /* [P+1]   E((i + 1/2) dt_eff)                         */
+    const long long* base;/* device step counter: the launch advances step base+i */
+    double* trace_v;      /* [K+1] whole-grid v_dr samples                       */
+    double* trace_n;      /* [K+1] whole-grid norm samples                       */
+    double* part;         /* [2][ntx] per-tile partial sums of row 0 / row 1     */
+    unsigned* ticket;     /* arrival counter of the row-0 CTAs                   */
+    int* err;             /* device error word (timeouts)                        */
+    int N, M, pitch, P;
+    int tile_m, chunk_n, ntx, nty;
+    T h, hh, nu, xi, c;   /* dt, dt/2, 1 + dt/2, 1 - dt/2, B dt/(4 dphi)         */
+    double vscale, nscale;/* pi sqrt(alpha) dphi, 2 pi sqrt(alpha) dphi          */
+};
+
+/* One plain application of T (start-up half step), unfused. */
+template <typename T>
+struct ApplyArgs {
+    const T* a;  const T* b;     /* state at t0                                */
+    const T* as; const T* bs;    /* stencil source                             */
+    T* an; T* bn;                /* output (may not alias the inputs)          */
+    const T* row_a0; const T* col_g; const T* col_bphi;
+    int N, M, pitch;
+    double E_start, E_end;
+    T h, hh, nu, xi, c;
+};
+
+struct FinalArgs {
+    const double* trace_v;
+    const double* trace_n;
+    long long k;          /* current step: samples 0..k are valid */
+    long long K, Kw, P;
+    double omega, dt_eff, inv_r1;
+    double* out;          /* [4]: A, vbar, max|norm-1|, nonfinite flag */
+};
+
+/* Kernel launchers (bte_kernels.cu). */
+template <typename T>
+int launch_init(T* a_w, T* b_w, const T* row_a0, const T* col_g, int N, int M, int pitch,
+                void* stream);
+template <typename T>
+int launch_apply(const ApplyArgs<T>& a, void* stream);
+template <typename T>
+int launch_step(const StepArgs<T>& a, int i, void* stream);
+template <typename T>
+int launch_observe(const T* a_w, const T* b_w, int M, int pitch, double vscale,
+                   double nscale, double* trace_v, double* trace_n, long long slot,
+                   void* stream);
+int launch_advance_base(long long* base, long long by, void* stream);
+int launch_finalize(const FinalArgs& a, void* stream);
+template <typename T>
+size_t step_smem_bytes(int tile_m);
+template <typename T>
+int step_kernel_configure(int tile_m);
+
+}  // namespace bte

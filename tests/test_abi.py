@@ -1,0 +1,80 @@
+"""CPU-side checks of the C ABI library: it loads without a GPU, exports every
+symbol the headers declare, and its host-only helpers (Miller Bessel ratios,
+time grid, parameter validation) are right."""
+import glob
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1401_6047_gb300 import bte
+from paper_1401_6047_gb300 import workloads as W
+from tests import analytic as an
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        names += re.findall(r"^BTE_API\s+[\w\s\*]+?\b(bte\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("bte_create", "bte_step", "bte_run", "bte_observables", "bte_destroy",
+                     "bte_get_state", "bte_set_state", "bte_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = bte.lib()
+    missing = [n for n in declared_symbols() if not hasattr(L, n)]
+    assert not missing, missing
+    assert "sm_103a" in bte.version()
+
+
+def test_miller_bessel_ratio_matches_scipy():
+    """The library's I_n/I_0 (Miller recurrence) against scipy.special.ive."""
+    for mu, nmax in [(0.5, 200), (1.0, 30), (2.0, 400), (20.0, 2048), (116.0, 119), (10.0, 4000)]:
+        r = bte.bessel_ratio(mu, nmax)
+        ref = an.bessel_ratio(mu, np.arange(nmax + 1))
+        big = ref > 1e-280
+        assert np.all(np.abs(r[big] - ref[big]) <= 1e-12 * ref[big] + 1e-300), (mu, nmax)
+        assert np.max(np.abs(r - ref)) < 1e-14
+        assert r[0] == 1.0
+
+
+def test_time_grid_closed_form():
+    p = W.c2()
+    dt, P, K, Kw = bte.time_grid(p)
+    assert P == round(2 * math.pi / (p.omega * p.dt)) == 6283
+    assert abs(dt - 2 * math.pi / (p.omega * P)) < 1e-18
+    assert K == 50 * P and Kw == 10 * P
+    q = W.Params(omega=0.0, E_omega=0.0, t_max=3.0, dt=1e-2, avg_window=1.0)
+    dt, P, K, Kw = bte.time_grid(q)
+    assert (dt, P, K, Kw) == (1e-2, 0, 300, 100)
+
+
+@pytest.mark.parametrize("bad", [dict(n_max=0), dict(m_points=2), dict(dt=0.0), dict(mu=0.0),
+                                 dict(alpha=-1.0), dict(omega=-2.0), dict(E_dc=float("inf")),
+                                 dict(phiy_max=-20.0), dict(avg_window=25.0), dict(precision=7)])
+def test_invalid_parameters_rejected_on_host(bad):
+    """Validation happens before any CUDA call, so it needs no GPU."""
+    with pytest.raises(bte.BteError) as e:
+        bte.workspace_size(W.c1_fp64().replace(**bad))
+    assert e.value.code == bte.EINVAL
+
+
+def test_workspace_size_covers_state():
+    p = W.c2()
+    n = bte.workspace_size(p)
+    assert n >= 8 * p.cells * 4
+    n64 = bte.workspace_size(p.replace(precision=W.FP64))
+    assert n64 >= 8 * p.cells * 8
+    with pytest.raises(bte.BteError):
+        bte.workspace_size(p, tile_m=30)
