@@ -174,8 +174,13 @@ int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L
     if (rc) return rc;
     L.elem = p->precision == BTE_FP64 ? 8 : 4;
     L.G = (int)(16 / L.elem);
-    const size_t smem = L.elem == 8 ? bte::step_smem_bytes<double>(L.tile_m)
-                                    : bte::step_smem_bytes<float>(L.tile_m);
+    const int max_tile = L.elem == 8 ? bte::step_max_tile<double>() : bte::step_max_tile<float>();
+    if (L.tile_m > max_tile) {
+        if (t && t->tile_m) return fail(BTE_EINVAL, "tile_m %d above %d for this precision", L.tile_m, max_tile);
+        L.tile_m = max_tile;
+    }
+    const size_t smem = L.elem == 8 ? bte::step_smem_bytes<double>(L.tile_m, L.chunk_n)
+                                    : bte::step_smem_bytes<float>(L.tile_m, L.chunk_n);
     if (smem > 227 * 1024)
         return fail(BTE_EINVAL, "tile_m %d needs %zu bytes of shared memory", L.tile_m, smem);
     const int M1 = p->m_points, N1 = p->n_max + 1;
@@ -233,6 +238,7 @@ struct bte_handle {
     long long k;   /* steps queued so far */
     long long base_host;
     int graph_len;
+    int grid;      /* persistent CTAs of the step kernel */
     cudaGraphExec_t graph;
     double r1;     /* I_1/I_0 */
     double dphi;
@@ -273,6 +279,7 @@ bte::StepArgs<T> step_args(const bte_handle* h) {
     a.chunk_n = L.chunk_n;
     a.ntx = L.ntx;
     a.nty = L.nty;
+    a.grid = h->grid;
     const double dt = h->tg.dt_eff;
     a.h = (T)dt;
     a.hh = (T)(0.5 * dt);
@@ -572,9 +579,19 @@ int bte_create_ex(const bte_params* p, void* stream, const bte_tuning* tune, voi
         }
         h->own_mem = true;
     }
-    rc = h->fp64 ? bte::step_kernel_configure<double>(h->L.tile_m)
-                 : bte::step_kernel_configure<float>(h->L.tile_m);
-    if (rc) return bail(fail(BTE_ECUDA, "kernel configure: %s", cudaGetErrorString((cudaError_t)rc)));
+    {
+        int bps = 0, dev = 0, sms = 0;
+        rc = h->fp64 ? bte::step_kernel_configure<double>(h->L.tile_m, h->L.chunk_n, &bps)
+                     : bte::step_kernel_configure<float>(h->L.tile_m, h->L.chunk_n, &bps);
+        if (rc)
+            return bail(fail(BTE_ECUDA, "kernel configure: %s", cudaGetErrorString((cudaError_t)rc)));
+        if (bps < 1) return bail(fail(BTE_EINVAL, "launch shape does not fit on an SM"));
+        CU(cudaGetDevice(&dev));
+        CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const long long items = (long long)h->L.ntx * h->L.nty;
+        const long long slots = (long long)bps * sms;
+        h->grid = (int)(items < slots ? items : slots);
+    }
     rc = h->fp64 ? upload_tables<double>(h) : upload_tables<float>(h);
     if (rc) return bail(rc);
     rc = h->fp64 ? initialise<double>(h, true, true) : initialise<float>(h, true, true);

@@ -40,6 +40,7 @@ struct StepArgs {
     int* err;             /* device error word (timeouts)                        */
     int N, M, pitch, P;
     int tile_m, chunk_n, ntx, nty;
+    int grid;             /* persistent CTAs; items are ntx * nty              */
     T h, hh, nu, xi, c;   /* dt, dt/2, 1 + dt/2, 1 - dt/2, B dt/(4 dphi)         */
     double vscale, nscale;/* pi sqrt(alpha) dphi, 2 pi sqrt(alpha) dphi          */
 };
@@ -80,8 +81,12 @@ int launch_observe(const T* a_w, const T* b_w, int M, int pitch, double vscale,
 int launch_advance_base(long long* base, long long by, void* stream);
 int launch_finalize(const FinalArgs& a, void* stream);
 template <typename T>
-size_t step_smem_bytes(int tile_m);
+size_t step_smem_bytes(int tile_m, int chunk_n);
 template <typename T>
-int step_kernel_configure(int tile_m);
+int step_block_threads(int tile_m);
+template <typename T>
+int step_max_tile();
+template <typename T>
+int step_kernel_configure(int tile_m, int chunk_n, int* blocks_per_sm);
 
 }  // namespace bte
