@@ -234,7 +234,7 @@ def run_ours(args):
     elem = 8 if args.precision == "fp64" else 4
     stream = torch.cuda.Stream(device=dev)
     solver = bte.Solver(p, stream=stream.cuda_stream, tile_m=args.tile_m, chunk_n=args.chunk_n,
-                        graph_steps=args.graph_steps)
+                        graph_steps=args.graph_steps, vec=args.vec)
     graph_len = min(args.graph_steps or 1024, K)
     launches_per_solve = 3 + K + (K // graph_len) + (1 if K % graph_len else 0) + 1
 
@@ -307,7 +307,7 @@ def run_ours(args):
     # table upload), run, observables (device -> host), destroy
     e2e = None
     if not args.no_e2e:
-        pitch = bte.launch_shape(p, args.tile_m, args.chunk_n)["pitch"]
+        pitch = bte.launch_shape(p, args.tile_m, args.chunk_n, args.vec)["pitch"]
         h2d = (p.n_max + 1) * elem + 2 * pitch * elem + 2 * (max(P, 1) + 1) * 8
         d2h = 4 * 8 + 2 * 8 + 4
         e2e_steps = max(1, min(args.steps, 3))
@@ -315,7 +315,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             with bte.Solver(p, tile_m=args.tile_m, chunk_n=args.chunk_n,
-                            graph_steps=args.graph_steps) as s2:
+                            graph_steps=args.graph_steps, vec=args.vec) as s2:
                 s2.run()
                 s2.observables()
         torch.cuda.synchronize()
@@ -379,6 +379,7 @@ def main():
     ap.add_argument("--tile-m", dest="tile_m", type=int, default=0)
     ap.add_argument("--chunk-n", dest="chunk_n", type=int, default=0)
     ap.add_argument("--graph-steps", dest="graph_steps", type=int, default=0)
+    ap.add_argument("--vec", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

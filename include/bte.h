@@ -103,10 +103,10 @@ typedef struct {
 
 /* Optional launch shape of the fused step kernel; 0 fields = automatic. */
 typedef struct {
-    int32_t tile_m;      /* phi_y columns per CTA (multiple of 4, 32..1024)  */
-    int32_t chunk_n;     /* harmonic rows per CTA (>= 4)                     */
+    int32_t tile_m;      /* phi_y columns per work item (multiple of 4, 32..1024) */
+    int32_t chunk_n;     /* harmonic rows per work item (>= 4)               */
     int32_t graph_steps; /* steps captured per CUDA graph replay (0 = auto)  */
-    int32_t reserved;
+    int32_t vec;         /* phi_y columns per thread: 2 or 4 (FP64: 2)      */
 } bte_tuning;
 
 typedef struct bte_handle bte_handle;

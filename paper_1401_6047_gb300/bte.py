@@ -51,7 +51,7 @@ class bte_obs(ctypes.Structure):
 
 class bte_tuning(ctypes.Structure):
     _fields_ = [("tile_m", ctypes.c_int32), ("chunk_n", ctypes.c_int32),
-                ("graph_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("graph_steps", ctypes.c_int32), ("vec", ctypes.c_int32)]
 
 
 _lib = None
@@ -127,9 +127,9 @@ def to_params(p) -> bte_params:
     return s
 
 
-def _tuning(tile_m=0, chunk_n=0, graph_steps=0):
+def _tuning(tile_m=0, chunk_n=0, graph_steps=0, vec=0):
     t = bte_tuning()
-    t.tile_m, t.chunk_n, t.graph_steps, t.reserved = int(tile_m), int(chunk_n), int(graph_steps), 0
+    t.tile_m, t.chunk_n, t.graph_steps, t.vec = int(tile_m), int(chunk_n), int(graph_steps), int(vec)
     return t
 
 
@@ -152,18 +152,18 @@ def time_grid(p):
     return dt.value, P.value, K.value, Kw.value
 
 
-def workspace_size(p, tile_m=0, chunk_n=0) -> int:
+def workspace_size(p, tile_m=0, chunk_n=0, vec=0) -> int:
     s = to_params(p)
-    t = _tuning(tile_m, chunk_n)
+    t = _tuning(tile_m, chunk_n, 0, vec)
     n = ctypes.c_size_t()
     _check(lib().bte_workspace_size(ctypes.byref(s), ctypes.byref(t), ctypes.byref(n)))
     return n.value
 
 
-def launch_shape(p, tile_m=0, chunk_n=0) -> dict:
+def launch_shape(p, tile_m=0, chunk_n=0, vec=0) -> dict:
     """tile_m, chunk_n, pitch, grid_x, grid_y the library picks for p."""
     s = to_params(p)
-    t = _tuning(tile_m, chunk_n)
+    t = _tuning(tile_m, chunk_n, 0, vec)
     v = [ctypes.c_int32() for _ in range(5)]
     _check(lib().bte_launch_shape(ctypes.byref(s), ctypes.byref(t), *(ctypes.byref(x) for x in v)))
     return dict(zip(("tile_m", "chunk_n", "pitch", "grid_x", "grid_y"), (x.value for x in v)))
@@ -195,11 +195,12 @@ class Solver:
     caller keeps alive while the solver exists."""
 
     def __init__(self, p, stream: int = 0, tile_m: int = 0, chunk_n: int = 0,
-                 graph_steps: int = 0, workspace: int = 0, workspace_bytes: int = 0):
+                 graph_steps: int = 0, workspace: int = 0, workspace_bytes: int = 0,
+                 vec: int = 0):
         self._lib = lib()
         self.params = to_params(p)
         self._h = ctypes.c_void_p()
-        t = _tuning(tile_m, chunk_n, graph_steps)
+        t = _tuning(tile_m, chunk_n, graph_steps, vec)
         _check(self._lib.bte_create_ex(ctypes.byref(self.params), ctypes.c_void_p(stream or None),
                                        ctypes.byref(t), ctypes.c_void_p(workspace or None),
                                        int(workspace_bytes), ctypes.byref(self._h)))

@@ -123,10 +123,14 @@ void miller_ratio(double x, int nmax, double* r) {
     for (int n = 0; n <= nmax; ++n) r[n] = I[n] / I[0];
 }
 
-int pick_tile(const bte_params* p, const bte_tuning* t, int& tile_m, int& chunk_n) {
+int pick_tile(const bte_params* p, const bte_tuning* t, int& tile_m, int& chunk_n, int& vec) {
     const int M1 = p->m_points, N1 = p->n_max + 1;
+    const bool fp64 = p->precision == BTE_FP64;
     tile_m = (t && t->tile_m) ? t->tile_m : 0;
     chunk_n = (t && t->chunk_n) ? t->chunk_n : 0;
+    vec = (t && t->vec) ? t->vec : (fp64 ? 2 : 4);
+    if (vec != 2 && vec != 4) return fail(BTE_EINVAL, "vec must be 2 or 4");
+    if (fp64 && vec != 2) return fail(BTE_EINVAL, "FP64 runs with vec = 2");
     if (tile_m) {
         if (tile_m % 4 || tile_m < 32 || tile_m > 1024)
             return fail(BTE_EINVAL, "tile_m must be a multiple of 4 in 32..1024");
@@ -152,7 +156,7 @@ int pick_tile(const bte_params* p, const bte_tuning* t, int& tile_m, int& chunk_
         if (chunk_n < 4) return fail(BTE_EINVAL, "chunk_n must be >= 4");
     } else {
         const int ntx = (M1 + tile_m - 1) / tile_m;
-        const int want = 4 * 152; /* enough CTAs for a few per SM */
+        const int want = 4 * 152; /* enough items for a few per SM */
         chunk_n = 64;
         while (chunk_n > 8 && (long long)ntx * ((N1 + chunk_n - 1) / chunk_n) < want) chunk_n /= 2;
     }
@@ -162,7 +166,7 @@ int pick_tile(const bte_params* p, const bte_tuning* t, int& tile_m, int& chunk_
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-    int G, pitch, tile_m, chunk_n, ntx, nty;
+    int G, H, pitch, tile_m, chunk_n, vec, ntx, nty;
     size_t elem;
     size_t off_state[8];
     size_t off_row_a0, off_col_g, off_col_bphi, off_ew, off_ef, off_tv, off_tn, off_part,
@@ -170,24 +174,26 @@ struct Layout {
 };
 
 int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L) {
-    int rc = pick_tile(p, t, L.tile_m, L.chunk_n);
+    int rc = pick_tile(p, t, L.tile_m, L.chunk_n, L.vec);
     if (rc) return rc;
     L.elem = p->precision == BTE_FP64 ? 8 : 4;
-    L.G = (int)(16 / L.elem);
-    const int max_tile = L.elem == 8 ? bte::step_max_tile<double>() : bte::step_max_tile<float>();
+    L.G = (int)(128 / L.elem);
+    L.H = (int)(16 / L.elem);
+    const int max_tile = L.elem == 8 ? bte::step_max_tile<double>(L.vec)
+                                     : bte::step_max_tile<float>(L.vec);
     if (L.tile_m > max_tile) {
         if (t && t->tile_m) return fail(BTE_EINVAL, "tile_m %d above %d for this precision", L.tile_m, max_tile);
         L.tile_m = max_tile;
     }
-    const size_t smem = L.elem == 8 ? bte::step_smem_bytes<double>(L.tile_m, L.chunk_n)
-                                    : bte::step_smem_bytes<float>(L.tile_m, L.chunk_n);
+    const size_t smem = L.elem == 8 ? bte::step_smem_bytes<double>(L.tile_m, L.chunk_n, L.vec)
+                                    : bte::step_smem_bytes<float>(L.tile_m, L.chunk_n, L.vec);
     if (smem > 227 * 1024)
         return fail(BTE_EINVAL, "tile_m %d needs %zu bytes of shared memory", L.tile_m, smem);
     const int M1 = p->m_points, N1 = p->n_max + 1;
     L.ntx = (M1 + L.tile_m - 1) / L.tile_m;
     L.nty = (N1 + L.chunk_n - 1) / L.chunk_n;
-    /* the last tile reads up to column G + ntx*tile_m + G - 1 */
-    L.pitch = (int)align_up((size_t)(L.ntx * L.tile_m + 2 * L.G), 32);
+    /* the last tile reads up to column G + ntx*tile_m + H - 1 */
+    L.pitch = (int)align_up((size_t)(L.G + L.ntx * L.tile_m + L.H), 32);
     size_t o = 0;
     const size_t arr = align_up((size_t)N1 * L.pitch * L.elem, 256);
     for (int q = 0; q < 8; ++q) {
@@ -239,7 +245,7 @@ struct bte_handle {
     long long base_host;
     int graph_len;
     int grid;      /* persistent CTAs of the step kernel */
-    cudaGraphExec_t graph;
+    cudaGraphExec_t graph[2]; /* graph_len steps starting on an even / odd step */
     double r1;     /* I_1/I_0 */
     double dphi;
     template <typename T>
@@ -279,6 +285,7 @@ bte::StepArgs<T> step_args(const bte_handle* h) {
     a.chunk_n = L.chunk_n;
     a.ntx = L.ntx;
     a.nty = L.nty;
+    a.vec = L.vec;
     a.grid = h->grid;
     const double dt = h->tg.dt_eff;
     a.h = (T)dt;
@@ -385,40 +392,53 @@ int initialise(bte_handle* h, bool full, bool sync) {
 }
 
 template <typename T>
-int enqueue_steps(bte_handle* h, long long n) {
+int capture_graph(bte_handle* h, int parity) {
     const bte::StepArgs<T> a = step_args<T>(h);
     long long* base = h->ptr<long long>(h->L.off_base);
-    if (h->graph_len > 1 && n >= h->graph_len && !h->graph) {
-        /* capture graph_len fused steps plus the counter update once */
-        cudaGraph_t g = nullptr;
-        CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-        int rc = 0;
-        for (int i = 0; i < h->graph_len && !rc; ++i) rc = bte::launch_step<T>(a, i, h->cap_stream);
-        if (!rc) rc = bte::launch_advance_base(base, h->graph_len, h->cap_stream);
-        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
-        if (rc || e != cudaSuccess) {
-            if (g) cudaGraphDestroy(g);
-            return fail(BTE_ECUDA, "graph capture failed: %s",
-                        cudaGetErrorString(e != cudaSuccess ? e : (cudaError_t)rc));
-        }
-        e = cudaGraphInstantiate(&h->graph, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-            h->graph = nullptr;
-            return fail(BTE_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
-        }
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = 0;
+    for (int i = 0; i < h->graph_len && !rc; ++i)
+        rc = bte::launch_step<T>(a, i, parity, i > 0, h->cap_stream);
+    if (!rc) rc = bte::launch_advance_base(base, h->graph_len, h->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (rc || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(BTE_ECUDA, "graph capture failed: %s",
+                    cudaGetErrorString(e != cudaSuccess ? e : (cudaError_t)rc));
     }
-    while (h->graph && n >= h->graph_len) {
-        CU(cudaGraphLaunch(h->graph, h->stream));
+    e = cudaGraphInstantiate(&h->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph[parity] = nullptr;
+        return fail(BTE_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    }
+    return BTE_OK;
+}
+
+/* Queues n steps: whole graphs of graph_len steps (one per parity of the
+ * first step, captured on first use), then single launches.  Launches after
+ * the first of a run use programmatic dependent launch. */
+template <typename T>
+int enqueue_steps(bte_handle* h, long long n) {
+    while (h->graph_len > 1 && n >= h->graph_len) {
+        const int par = (int)(h->k & 1);
+        if (!h->graph[par]) {
+            int rc = capture_graph<T>(h, par);
+            if (rc) return rc;
+        }
+        CU(cudaGraphLaunch(h->graph[par], h->stream));
         n -= h->graph_len;
         h->k += h->graph_len;
     }
     if (n > 0) {
+        const bte::StepArgs<T> a = step_args<T>(h);
+        const int par = (int)(h->k & 1);
         for (long long i = 0; i < n; ++i) {
-            int rc = bte::launch_step<T>(a, (int)i, h->stream);
+            int rc = bte::launch_step<T>(a, (int)i, par, i > 0, h->stream);
             if (rc) return fail(BTE_ECUDA, "step kernel: %s", cudaGetErrorString((cudaError_t)rc));
         }
-        int rc = bte::launch_advance_base(base, n, h->stream);
+        int rc = bte::launch_advance_base(h->ptr<long long>(h->L.off_base), n, h->stream);
         if (rc) return fail(BTE_ECUDA, "counter kernel: %s", cudaGetErrorString((cudaError_t)rc));
         h->k += n;
     }
@@ -581,8 +601,8 @@ int bte_create_ex(const bte_params* p, void* stream, const bte_tuning* tune, voi
     }
     {
         int bps = 0, dev = 0, sms = 0;
-        rc = h->fp64 ? bte::step_kernel_configure<double>(h->L.tile_m, h->L.chunk_n, &bps)
-                     : bte::step_kernel_configure<float>(h->L.tile_m, h->L.chunk_n, &bps);
+        rc = h->fp64 ? bte::step_kernel_configure<double>(h->L.tile_m, h->L.chunk_n, h->L.vec, &bps)
+                     : bte::step_kernel_configure<float>(h->L.tile_m, h->L.chunk_n, h->L.vec, &bps);
         if (rc)
             return bail(fail(BTE_ECUDA, "kernel configure: %s", cudaGetErrorString((cudaError_t)rc)));
         if (bps < 1) return bail(fail(BTE_EINVAL, "launch shape does not fit on an SM"));
@@ -722,7 +742,8 @@ int bte_set_step(bte_handle* h, int64_t k, const double* v, const double* norm) 
 void bte_destroy(bte_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    if (h->graph) cudaGraphExecDestroy(h->graph);
+    for (int q = 0; q < 2; ++q)
+        if (h->graph[q]) cudaGraphExecDestroy(h->graph[q]);
     if (h->own_mem && h->mem) cudaFree(h->mem);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);

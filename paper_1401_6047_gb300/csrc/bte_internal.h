@@ -4,8 +4,9 @@
  *
  * Device layout of one grid array (a or b, whole or fractional grid):
  *   rows n = 0..N (N = n_max), row pitch `pitch` elements, column m of the
- *   phi_y grid at physical index G + m with G = 16 / sizeof(T) zero ghost
- *   columns on the left; columns G+M+1 .. pitch-1 are zero ghosts too.
+ *   phi_y grid at physical index G + m with G = 128 / sizeof(T) zero ghost
+ *   columns on the left (so tiles start on 128-byte lines); columns
+ *   G+M+1 .. pitch-1 are zero ghosts too.
  *   Ghost columns are written once (zero) and never again, so the stencil
  *   at m = 0 and m = M reads the boundary value 0 of Eqs. a_boundary and
  *   b_boundary without a branch.  Rows outside 0..N are never stored; the
@@ -19,6 +20,15 @@ namespace bte {
 
 /* value stored in the device error word when a bounded wait gives up */
 constexpr int kErrTimeout = 1;
+
+/* Column layout constants: G zero ghost columns before m = 0 (128 bytes),
+ * H halo columns streamed on each side of a tile (16 bytes, the TMA
+ * granule). */
+template <typename T>
+struct Cols {
+    static constexpr int G = 128 / (int)sizeof(T);
+    static constexpr int H = 16 / (int)sizeof(T);
+};
 
 /* Arguments of the fused step kernel (one leap-frog step). */
 template <typename T>
@@ -40,6 +50,7 @@ struct StepArgs {
     int* err;             /* device error word (timeouts)                        */
     int N, M, pitch, P;
     int tile_m, chunk_n, ntx, nty;
+    int vec;              /* phi_y columns per compute thread (2 or 4)         */
     int grid;             /* persistent CTAs; items are ntx * nty              */
     T h, hh, nu, xi, c;   /* dt, dt/2, 1 + dt/2, 1 - dt/2, B dt/(4 dphi)         */
     double vscale, nscale;/* pi sqrt(alpha) dphi, 2 pi sqrt(alpha) dphi          */
@@ -72,8 +83,11 @@ int launch_init(T* a_w, T* b_w, const T* row_a0, const T* col_g, int N, int M, i
                 void* stream);
 template <typename T>
 int launch_apply(const ApplyArgs<T>& a, void* stream);
+/* Launches step base+i; `parity` = (base & 1) as known to the host, so the
+ * ping-pong set is chosen without a device read.  `pdl` enables
+ * programmatic dependent launch (the prologue overlaps the previous step). */
 template <typename T>
-int launch_step(const StepArgs<T>& a, int i, void* stream);
+int launch_step(const StepArgs<T>& a, int i, int parity, bool pdl, void* stream);
 template <typename T>
 int launch_observe(const T* a_w, const T* b_w, int M, int pitch, double vscale,
                    double nscale, double* trace_v, double* trace_n, long long slot,
@@ -81,12 +95,12 @@ int launch_observe(const T* a_w, const T* b_w, int M, int pitch, double vscale,
 int launch_advance_base(long long* base, long long by, void* stream);
 int launch_finalize(const FinalArgs& a, void* stream);
 template <typename T>
-size_t step_smem_bytes(int tile_m, int chunk_n);
+size_t step_smem_bytes(int tile_m, int chunk_n, int vec);
 template <typename T>
-int step_block_threads(int tile_m);
+int step_block_threads(int tile_m, int vec);
 template <typename T>
-int step_max_tile();
+int step_max_tile(int vec);
 template <typename T>
-int step_kernel_configure(int tile_m, int chunk_n, int* blocks_per_sm);
+int step_kernel_configure(int tile_m, int chunk_n, int vec, int* blocks_per_sm);
 
 }  // namespace bte

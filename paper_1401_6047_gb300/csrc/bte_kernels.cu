@@ -24,7 +24,7 @@ using namespace dev;
 template <typename T>
 __global__ void init_kernel(T* a_w, T* b_w, const T* row_a0, const T* col_g, int N, int M,
                             int pitch) {
-    constexpr int G = 16 / (int)sizeof(T);
+    constexpr int G = Cols<T>::G;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
     if (m > M || n > N) return;
@@ -40,7 +40,7 @@ __device__ __forceinline__ T ld_or0(const T* x, int n, int c, int N, int pitch) 
 
 template <typename T>
 __global__ void apply_kernel(ApplyArgs<T> A) {
-    constexpr int G = 16 / (int)sizeof(T);
+    constexpr int G = Cols<T>::G;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
     if (m > A.M || n > A.N) return;
@@ -69,7 +69,7 @@ __global__ void apply_kernel(ApplyArgs<T> A) {
 template <typename T>
 __global__ void observe_kernel(const T* a_w, const T* b_w, int M, int pitch, double vscale,
                                double nscale, double* trace_v, double* trace_n, long long slot) {
-    constexpr int G = 16 / (int)sizeof(T);
+    constexpr int G = Cols<T>::G;
     __shared__ double red[32];
     double sn = 0, sv = 0;
     for (int m = threadIdx.x; m <= M; m += blockDim.x) {

@@ -16,11 +16,11 @@
  * the new whole-grid row j (its columns plus one halo column per side) and
  * then the new fractional row j-1, which needs the new whole rows j-2 and j.
  *
- * Threads.  Compute thread t owns the column pair (2t, 2t+1) of the tile.
- * One extra warp (the producer) issues the TMA bulk copies that stream the
- * old fractional and whole rows into a ring of RS shared-memory stages
- * (cp.async.bulk + mbarrier, RS-2 rows ahead of use, continuing across
- * items), and computes the two halo cells of each new whole row.
+ * Threads.  Compute thread t owns V consecutive columns (V = 2 or 4) of the
+ * tile.  One extra warp (the producer) issues the TMA bulk copies that
+ * stream the old fractional and whole rows into a ring of RS shared-memory
+ * stages (cp.async.bulk + mbarrier, RS-2 rows ahead of use, continuing
+ * across items), and computes the two halo cells of each new whole row.
  *
  * Data reuse.  Every old fractional row is read from shared memory once per
  * thread when it arrives; its own values and central differences stay in
@@ -28,6 +28,10 @@
  * shared memory once (for the neighbours' differences) and straight from
  * registers to global memory; the new fractional row goes from registers to
  * global memory.  One __syncthreads per row.
+ *
+ * Launch.  Programmatic dependent launch: the prologue (barrier set-up,
+ * drive values) runs while the previous step drains; griddepcontrol.wait
+ * precedes the first read of the state.
  *
  * Observables (Sec. 2, Eqs. v_dr_generic and norm_in_phi): items that own
  * rows 0 and 1 reduce sum_m a_{0,m} and sum_m b_{1,m} in FP64; the last of
@@ -50,42 +54,28 @@ namespace {
 
 using namespace dev;
 
-/* largest block: 512 compute threads + producer warp in FP32; FP64 tiles
- * stop at 512 columns (256 + 32 threads) to leave room for its registers */
-template <typename T>
-struct MaxBlock {
-    static constexpr int value = sizeof(T) == 4 ? 544 : 288;
-};
-
-template <typename T>
-struct Vec2;
-template <>
-struct Vec2<float> {
-    using type = float2;
-};
-template <>
-struct Vec2<double> {
-    using type = double2;
-};
-
 template <typename T>
 struct StepCfg {
-    static constexpr int H = 16 / (int)sizeof(T); /* zero ghost / halo columns = 16 bytes */
+    static constexpr int H = Cols<T>::H;
+    static constexpr int G = Cols<T>::G;
     static constexpr int RS = sizeof(T) == 4 ? 8 : 6; /* TMA ring stages */
 };
 
-template <typename T>
-__host__ __device__ inline int compute_threads(int tile_m) {
-    return tile_m / 2;
-}
+/* largest block: 512 compute threads + producer warp for FP32 with V = 2,
+ * 256 + 32 otherwise (FP64 needs the registers) */
+template <typename T, int V>
+struct MaxBlock {
+    static constexpr int value = (sizeof(T) == 4 && V == 2) ? 544 : 288;
+};
+
 __host__ __device__ inline int round_warp(int n) { return (n + 31) / 32 * 32; }
 
 template <typename T>
-__host__ __device__ inline size_t smem_layout(int tile_m, int chunk_n, size_t* offN, size_t* offR,
-                                              size_t* offBar, size_t* offRed) {
+__host__ __device__ inline size_t smem_layout(int tile_m, int chunk_n, int V, size_t* offN,
+                                              size_t* offR, size_t* offBar, size_t* offRed) {
     constexpr int H = StepCfg<T>::H, RS = StepCfg<T>::RS;
     const size_t LW = (size_t)tile_m + 2 * H;
-    const size_t WN = (size_t)tile_m + 4;
+    const size_t WN = (size_t)tile_m + 2 * V;
     size_t o = 2 * (size_t)RS * 2 * LW * sizeof(T); /* old fractional + old whole rows */
     *offN = o;
     o += 2 * 2 * WN * sizeof(T); /* new whole rows, 2 slots x (a, b) */
@@ -100,24 +90,87 @@ __host__ __device__ inline size_t smem_layout(int tile_m, int chunk_n, size_t* o
     return o;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(MaxBlock<T>::value) fused_step_kernel(StepArgs<T> A, int launch_i) {
-    using V2 = typename Vec2<T>::type;
+/* V consecutive values at p (vector loads; p is aligned to V elements or 16 bytes). */
+template <typename T, int V>
+__device__ __forceinline__ void ld_own(const T* p, T (&x)[V]) {
+    if constexpr (sizeof(T) * V == 8) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        x[0] = v.x;
+        x[1] = v.y;
+    } else if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        x[0] = v.x;
+        x[1] = v.y;
+        x[2] = v.z;
+        x[3] = v.w;
+    } else {
+#pragma unroll
+        for (int e = 0; e < V; e += 2) {
+            const double2 v = *reinterpret_cast<const double2*>(p + e);
+            x[e] = v.x;
+            x[e + 1] = v.y;
+        }
+    }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void st_own(T* p, const T (&x)[V]) {
+    if constexpr (sizeof(T) * V == 8) {
+        *reinterpret_cast<float2*>(p) = make_float2(x[0], x[1]);
+    } else if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < V; e += 2)
+            *reinterpret_cast<double2*>(p + e) = make_double2(x[e], x[e + 1]);
+    }
+}
+
+/* Left and right neighbours p[-1], p[V] of a group. */
+template <typename T, int V>
+__device__ __forceinline__ void neighbours(const T* p, T& left, T& right) {
+    if constexpr (sizeof(T) == 4) {
+        left = reinterpret_cast<const float2*>(p - 2)->y;
+        right = reinterpret_cast<const float2*>(p + V)->x;
+    } else {
+        left = p[-1];
+        right = p[V];
+    }
+}
+
+/* Central differences of a group from its own values and neighbours. */
+template <typename T, int V>
+__device__ __forceinline__ void diffs(const T (&own)[V], T left, T right, T (&d)[V]) {
+    d[0] = own[1] - left;
+#pragma unroll
+    for (int e = 1; e < V - 1; ++e) d[e] = own[e + 1] - own[e - 1];
+    d[V - 1] = right - own[V - 2];
+}
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(MaxBlock<T, V>::value)
+    fused_step_kernel(StepArgs<T> A, int launch_i, int parity) {
     constexpr int H = StepCfg<T>::H;
+    constexpr int G = StepCfg<T>::G;
     constexpr int RS = StepCfg<T>::RS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
 
     const int Wt = A.tile_m;
-    const int NT = compute_threads<T>(Wt);
+    const int NT = Wt / V;
     const int NTr = round_warp(NT);
     const int LW = Wt + 2 * H;
-    const int WN = Wt + 4;
+    const int WN = Wt + 2 * V;
     size_t offN, offR, offBar, offRed;
-    smem_layout<T>(Wt, A.chunk_n, &offN, &offR, &offBar, &offRed);
-    T* sF = reinterpret_cast<T*>(smem_raw);             /* [RS][2][LW] */
-    T* sW = sF + (size_t)RS * 2 * LW;                   /* [RS][2][LW] */
-    T* sN = reinterpret_cast<T*>(smem_raw + offN);      /* [2][2][WN]  */
-    T* sR = reinterpret_cast<T*>(smem_raw + offR);      /* [chunk_n+4] */
+    smem_layout<T>(Wt, A.chunk_n, V, &offN, &offR, &offBar, &offRed);
+    T* sF = reinterpret_cast<T*>(smem_raw);        /* [RS][2][LW] */
+    T* sW = sF + (size_t)RS * 2 * LW;              /* [RS][2][LW] */
+    T* sN = reinterpret_cast<T*>(smem_raw + offN); /* [2][2][WN]  */
+    T* sR = reinterpret_cast<T*>(smem_raw + offR); /* [chunk_n+4] */
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + offBar);
     double* red = reinterpret_cast<double*>(smem_raw + offRed);
 
@@ -126,9 +179,20 @@ __global__ void __launch_bounds__(MaxBlock<T>::value) fused_step_kernel(StepArgs
     const bool is_prod = tid >= NTr;
     const int lane = tid & 31;
     const int N = A.N, M = A.M, pitch = A.pitch;
+    const int ntx = A.ntx;
+    const int items = A.ntx * A.nty;
+    const int cur = (parity + launch_i) & 1, nxt = cur ^ 1;
+    const uint32_t rowbytes = (uint32_t)(LW * sizeof(T));
 
-    const long long k = *A.base + launch_i;
-    const int cur = (int)(k & 1), nxt = cur ^ 1;
+    pdl_trigger();
+    if (tid == NTr) {
+        for (int s = 0; s < RS; ++s) mbar_init(smem_u32(&bar[s]), 1);
+        fence_proxy_async_smem();
+    }
+    /* new-row buffers: entries outside the tile's columns +-1 stay zero */
+    for (int q = tid; q < 4 * WN; q += blockDim.x) sN[q] = (T)0;
+
+    const long long k = *A.base + launch_i; /* only the counter kernel moves base */
     const int kk = A.P > 0 ? (int)(k % A.P) : 0;
     const T Ews = (T)A.e_whole[kk], Ewe = (T)A.e_whole[kk + 1];
     const T Efs = (T)A.e_frac[kk], Efe = (T)A.e_frac[kk + 1];
@@ -138,106 +202,100 @@ __global__ void __launch_bounds__(MaxBlock<T>::value) fused_step_kernel(StepArgs
     const T* gWa = A.a_w[cur];
     const T* gWb = A.b_w[cur];
     T* oWa = A.a_w[nxt];
-    T* oWb = A.b_w[nxt];
     T* oFa = A.a_f[nxt];
-    T* oFb = A.b_f[nxt];
-    const int ntx = A.ntx;
-    const int items = A.ntx * A.nty;
-    const uint32_t rowbytes = (uint32_t)(LW * sizeof(T));
-
-    if (tid == NTr) {
-        for (int s = 0; s < RS; ++s) mbar_init(smem_u32(&bar[s]), 1);
-        fence_proxy_async_smem();
-    }
-    /* new-row buffers: index 0 and WN-1 are never written and stay zero */
-    for (int q = tid; q < 4 * WN; q += blockDim.x) sN[q] = (T)0;
+    const size_t dWb = (size_t)(A.b_w[nxt] - oWa), dFb = (size_t)(A.b_f[nxt] - oFa);
     __syncthreads();
 
-    /* ---- producer state: global stage sequence across this CTA's items ---- */
-    int p_item = blockIdx.x; /* item whose stages are being issued */
-    int p_s = 0;             /* next stage of p_item                 */
-    long long issued = 0;    /* stages issued so far                 */
-    long long freed = 0;     /* stages whose slots may be reused     */
-    auto item_rows = [&](int q, int& n0, int& n1) {
-        const int ty = q / ntx;
-        n0 = ty * A.chunk_n;
-        n1 = min(n0 + A.chunk_n, N + 1);
+    /* everything below reads the previous step's state */
+    pdl_wait();
+
+    /* ---- producer: issues the global stage sequence of this CTA's items ---- */
+    int p_item = blockIdx.x, p_s = 0, p_S = 0, p_n0 = 0, p_n1 = 0;
+    size_t p_col0 = 0;
+    int p_slot = 0;
+    long long p_issued = 0, p_freed = 0;
+    auto p_load_item = [&]() {
+        const int ty = p_item / ntx;
+        p_n0 = ty * A.chunk_n;
+        p_n1 = min(p_n0 + A.chunk_n, N + 1);
+        p_S = p_n1 - p_n0 + 4;
+        p_col0 = (size_t)(p_item - ty * ntx) * Wt + (G - H);
     };
-    /* issue as many stages as the ring allows (producer lane 0 only) */
     auto pump = [&]() {
-        while (p_item < items && issued < freed + RS) {
-            int n0, n1;
-            item_rows(p_item, n0, n1);
-            const int S = n1 - n0 + 4; /* rows n0-2 .. n1+1 */
-            const int row = n0 - 2 + p_s;
-            const int slot = (int)(issued % RS);
-            const uint32_t mb = smem_u32(&bar[slot]);
+        while (p_item < items && p_issued < p_freed + RS) {
+            const int row = p_n0 - 2 + p_s;
+            const uint32_t mb = smem_u32(&bar[p_slot]);
             if (row < 0 || row > N) {
                 mbar_arrive(mb);
             } else {
-                const int tx = p_item % ntx;
-                const int col0 = tx * Wt; /* = first owned physical column - H */
-                const bool wneed = row >= n0 - 1 && row <= n1;
+                const bool wneed = row >= p_n0 - 1 && row <= p_n1;
                 mbar_arrive_tx(mb, rowbytes * (wneed ? 4u : 2u));
-                const size_t off = (size_t)row * pitch + col0;
-                T* dF = sF + (size_t)slot * 2 * LW;
+                const size_t off = (size_t)row * pitch + p_col0;
+                T* dF = sF + (size_t)p_slot * 2 * LW;
                 bulk_g2s(smem_u32(dF), gFa + off, rowbytes, mb);
                 bulk_g2s(smem_u32(dF + LW), gFb + off, rowbytes, mb);
                 if (wneed) {
-                    T* dW = sW + (size_t)slot * 2 * LW;
+                    T* dW = sW + (size_t)p_slot * 2 * LW;
                     bulk_g2s(smem_u32(dW), gWa + off, rowbytes, mb);
                     bulk_g2s(smem_u32(dW + LW), gWb + off, rowbytes, mb);
                 }
             }
-            ++issued;
-            if (++p_s == S) {
+            ++p_issued;
+            p_slot = (p_slot + 1 == RS) ? 0 : p_slot + 1;
+            if (++p_s == p_S) {
                 p_s = 0;
                 p_item += gridDim.x;
+                if (p_item < items) p_load_item();
             }
         }
     };
-    if (tid == NTr) pump();
+    if (tid == NTr && p_item < items) {
+        p_load_item();
+        pump();
+    }
 
     bool timed_out = false;
     long long cbase = 0; /* global stage index of the current item's stage 0 */
+    int c_slot = 0;      /* ring slot of the stage being consumed         */
+    uint32_t c_phase = 0;
 
     for (int q = blockIdx.x; q < items; q += gridDim.x) {
-        const int tx = q % ntx;
-        int n0, n1;
-        item_rows(q, n0, n1);
+        const int ty = q / ntx;
+        const int tx = q - ty * ntx;
+        const int n0 = ty * A.chunk_n;
+        const int n1 = min(n0 + A.chunk_n, N + 1);
         const int S = n1 - n0 + 4;
-        const int p0 = H + tx * Wt; /* physical column of the tile's first column */
+        const int p0 = G + tx * Wt; /* physical column of the tile's first column */
 
-        __syncthreads(); /* the previous item's last row is done with sR and sN */
-        /* row factors sigma_n I_n/I_0/pi of rows n0-1 .. n1 */
+        __syncthreads(); /* the previous item is done with sR and sN */
         for (int r = tid; r < n1 - n0 + 2; r += blockDim.x) {
             const int n = n0 - 1 + r;
             sR[r] = (n >= 0 && n <= N) ? A.row_a0[n] : (T)0;
         }
 
-        /* per-column constants of the thread's pair */
-        const int c = p0 + 2 * tid;         /* physical column of the pair   */
-        const int lc = H + 2 * tid;         /* its index in a streamed row   */
-        const bool ok0 = is_comp && (c - H) <= M;
-        const bool ok1 = is_comp && (c + 1 - H) <= M;
-        T g0 = 0, g1 = 0, bp0 = 0, bp1 = 0;
-        if (ok0) {
-            g0 = A.col_g[c];
-            bp0 = A.col_bphi[c];
+        /* per-column constants of the thread's V columns */
+        const int c = p0 + V * tid; /* physical column of the group      */
+        const int lc = H + V * tid; /* its index in a streamed row       */
+        const int ln = V + V * tid; /* its index in a new whole row      */
+        bool ok[V];
+        T g[V], ws[V], we[V], fs[V], fe[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            ok[e] = is_comp && (c + e - G) <= M;
+            const T bp = ok[e] ? A.col_bphi[c + e] : (T)0;
+            g[e] = ok[e] ? A.col_g[c + e] : (T)0;
+            ws[e] = (Ews + bp) * hh;
+            we[e] = (Ewe + bp) * hh;
+            fs[e] = (Efs + bp) * hh;
+            fe[e] = (Efe + bp) * hh;
         }
-        if (ok1) {
-            g1 = A.col_g[c + 1];
-            bp1 = A.col_bphi[c + 1];
-        }
-        const T ws0 = (Ews + bp0) * hh, ws1 = (Ews + bp1) * hh;
-        const T we0 = (Ewe + bp0) * hh, we1 = (Ewe + bp1) * hh;
-        const T fs0 = (Efs + bp0) * hh, fs1 = (Efs + bp1) * hh;
-        const T fe0 = (Efe + bp0) * hh, fe1 = (Efe + bp1) * hh;
+        const bool all_ok = ok[V - 1];
 
         /* producer lanes 0/1: the halo columns p0-1 and p0+Wt of new whole rows */
         const int hcol = (lane == 0) ? p0 - 1 : p0 + Wt;
-        const bool hok = is_prod && lane < 2 && (hcol - H) >= 0 && (hcol - H) <= M;
+        const bool hok = is_prod && lane < 2 && (hcol - G) >= 0 && (hcol - G) <= M;
         const int hlc = hcol - (p0 - H);
+        const int hidx = (lane == 0) ? V - 1 : V + Wt;
         T hg = 0, hbs = 0, hbe = 0;
         if (hok) {
             hg = A.col_g[hcol];
@@ -247,148 +305,150 @@ __global__ void __launch_bounds__(MaxBlock<T>::value) fused_step_kernel(StepArgs
         }
         __syncthreads(); /* sR ready */
 
-        /* rolling windows (registers): old fractional rows j-1, j (own pair
-         * and central differences), central differences of new whole rows
-         * j-2, j-1 */
-        V2 fa_m1 = {0, 0}, fb_m1 = {0, 0}, fa_0 = {0, 0}, fb_0 = {0, 0};
-        V2 dfa_m1 = {0, 0}, dfb_m1 = {0, 0}, dfa_0 = {0, 0}, dfb_0 = {0, 0};
-        V2 dwa_m2 = {0, 0}, dwb_m2 = {0, 0}, dwa_m1 = {0, 0}, dwb_m1 = {0, 0};
+        /* rolling windows (registers): old fractional rows j-1, j (own
+         * values and central differences), central differences of new whole
+         * rows j-2, j-1 */
+        T fa_m1[V], fb_m1[V], fa_0[V], fb_0[V];
+        T dfa_m1[V], dfb_m1[V], dfa_0[V], dfb_0[V];
+        T dwa_m2[V], dwb_m2[V], dwa_m1[V], dwb_m1[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            fa_m1[e] = fb_m1[e] = fa_0[e] = fb_0[e] = (T)0;
+            dfa_m1[e] = dfb_m1[e] = dfa_0[e] = dfb_0[e] = (T)0;
+            dwa_m2[e] = dwb_m2[e] = dwa_m1[e] = dwb_m1[e] = (T)0;
+        }
         double part_n = 0.0, part_v = 0.0;
+        int slot_m1 = 0, slot_m2 = 0; /* ring slots of the two previous stages */
 
-        /* stages 0 and 1 (old rows n0-2, n0-1) are consumed like row j+1 of
-         * iterations n0-3 and n0-2, which only load */
+        /* stages 0 and 1 (old rows n0-2, n0-1) are consumed as row j+1 of the
+         * load-only iterations j = n0-3, n0-2 */
         for (int j = n0 - 3; j <= n1; ++j) {
-            const int si = j - n0 + 3; /* stage holding old row j+1 */
-            const long long g = cbase + si;
-            const int slot = (int)(g % RS);
-            if (!mbar_wait(smem_u32(&bar[slot]), (uint32_t)((g / RS) & 1))) timed_out = true;
+            if (!mbar_wait(smem_u32(&bar[c_slot]), c_phase)) timed_out = true;
+            const T* ra = sF + (size_t)c_slot * 2 * LW; /* old fractional row j+1 */
 
-            /* old fractional row j+1: own pair and central differences */
-            V2 fa_p1 = {0, 0}, fb_p1 = {0, 0}, dfa_p1 = {0, 0}, dfb_p1 = {0, 0};
+            T fa_p1[V], fb_p1[V], dfa_p1[V], dfb_p1[V];
             if (j + 1 >= 0 && j + 1 <= N && is_comp) {
-                const T* ra = sF + (size_t)slot * 2 * LW;
-                const T* rb = ra + LW;
-                const V2 la = *reinterpret_cast<const V2*>(ra + lc - 2);
-                const V2 oa = *reinterpret_cast<const V2*>(ra + lc);
-                const V2 pa = *reinterpret_cast<const V2*>(ra + lc + 2);
-                const V2 lb = *reinterpret_cast<const V2*>(rb + lc - 2);
-                const V2 ob = *reinterpret_cast<const V2*>(rb + lc);
-                const V2 pb = *reinterpret_cast<const V2*>(rb + lc + 2);
-                fa_p1 = oa;
-                fb_p1 = ob;
-                dfa_p1.x = oa.y - la.y;
-                dfa_p1.y = pa.x - oa.x;
-                dfb_p1.x = ob.y - lb.y;
-                dfb_p1.y = pb.x - ob.x;
+                T l, r;
+                ld_own<T, V>(ra + lc, fa_p1);
+                neighbours<T, V>(ra + lc, l, r);
+                diffs<T, V>(fa_p1, l, r, dfa_p1);
+                ld_own<T, V>(ra + LW + lc, fb_p1);
+                neighbours<T, V>(ra + LW + lc, l, r);
+                diffs<T, V>(fb_p1, l, r, dfb_p1);
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e) fa_p1[e] = fb_p1[e] = dfa_p1[e] = dfb_p1[e] = (T)0;
             }
 
             if (j >= n0 - 1) {
                 /* ---- new whole-grid row j ---- */
-                const bool wrow = j >= 0 && j <= N;
-                V2 wa_n = {0, 0}, wb_n = {0, 0};
-                if (wrow) {
-                    const int sw = (int)((cbase + si - 1) % RS); /* stage of old row j */
+                const bool wrow_ok = j >= 0 && j <= N;
+                T wa_n[V], wb_n[V];
+                T* na = sN + (size_t)(j & 1) * 2 * WN;
+                if (wrow_ok) {
                     const T nf = (T)j;
                     const T chi = (j == 1) ? (T)2 : (T)1;
                     const T ha0 = h * sR[j - n0 + 1];
+                    const T* wa = sW + (size_t)slot_m1 * 2 * LW; /* old whole row j */
                     if (is_comp) {
-                        const T* wa = sW + (size_t)sw * 2 * LW;
-                        const V2 oa = *reinterpret_cast<const V2*>(wa + lc);
-                        const V2 ob = *reinterpret_cast<const V2*>(wa + LW + lc);
-                        T an, bn;
-                        cn_cell<T>(oa.x, ob.x, cc * (dfb_p1.x - dfb_m1.x),
-                                   cc * (chi * dfa_m1.x - dfa_p1.x), ha0 * g0, nf * ws0,
-                                   nf * we0, nu, xi, h, an, bn);
-                        wa_n.x = ok0 ? an : (T)0;
-                        wb_n.x = (ok0 && j > 0) ? bn : (T)0;
-                        cn_cell<T>(oa.y, ob.y, cc * (dfb_p1.y - dfb_m1.y),
-                                   cc * (chi * dfa_m1.y - dfa_p1.y), ha0 * g1, nf * ws1,
-                                   nf * we1, nu, xi, h, an, bn);
-                        wa_n.y = ok1 ? an : (T)0;
-                        wb_n.y = (ok1 && j > 0) ? bn : (T)0;
-                        T* na = sN + (size_t)(j & 1) * 2 * WN;
-                        *reinterpret_cast<V2*>(na + 2 + 2 * tid) = wa_n;
-                        *reinterpret_cast<V2*>(na + WN + 2 + 2 * tid) = wb_n;
+                        T oa[V], ob[V];
+                        ld_own<T, V>(wa + lc, oa);
+                        ld_own<T, V>(wa + LW + lc, ob);
+#pragma unroll
+                        for (int e = 0; e < V; ++e) {
+                            T an, bn;
+                            cn_cell<T>(oa[e], ob[e], cc * (dfb_p1[e] - dfb_m1[e]),
+                                       cc * (chi * dfa_m1[e] - dfa_p1[e]), ha0 * g[e], nf * ws[e],
+                                       nf * we[e], nu, xi, h, an, bn);
+                            wa_n[e] = ok[e] ? an : (T)0;
+                            wb_n[e] = (ok[e] && j > 0) ? bn : (T)0;
+                        }
+                        st_own<T, V>(na + ln, wa_n);
+                        st_own<T, V>(na + WN + ln, wb_n);
                         if (j >= n0 && j < n1) {
-                            const size_t go = (size_t)j * pitch + c;
-                            if (ok1) {
-                                *reinterpret_cast<V2*>(oWa + go) = wa_n;
-                                *reinterpret_cast<V2*>(oWb + go) = wb_n;
-                            } else if (ok0) {
-                                oWa[go] = wa_n.x;
-                                oWb[go] = wb_n.x;
+                            T* wrow = oWa + (size_t)j * pitch + c;
+                            if (all_ok) {
+                                st_own<T, V>(wrow, wa_n);
+                                st_own<T, V>(wrow + dWb, wb_n);
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < V; ++e)
+                                    if (ok[e]) {
+                                        wrow[e] = wa_n[e];
+                                        wrow[dWb + e] = wb_n[e];
+                                    }
                             }
                         }
-                        if (n0 == 0) {
-                            if (j == 0) part_n += (double)wa_n.x + (double)wa_n.y;
-                            if (j == 1) part_v += (double)wb_n.x + (double)wb_n.y;
+                        if (n0 == 0 && j <= 1) {
+#pragma unroll
+                            for (int e = 0; e < V; ++e) {
+                                if (j == 0) part_n += (double)wa_n[e];
+                                if (j == 1) part_v += (double)wb_n[e];
+                            }
                         }
                     } else if (is_prod && lane < 2) {
                         T an = 0, bn = 0;
                         if (hok) {
-                            const T* fd_a = sF + (size_t)((cbase + si - 2) % RS) * 2 * LW;
-                            const T* fu_a = sF + (size_t)slot * 2 * LW;
+                            const T* fd = sF + (size_t)slot_m2 * 2 * LW; /* old frac row j-1 */
                             const bool dn = j - 1 >= 0, up = j + 1 <= N;
-                            const T Dad = dn ? fd_a[hlc + 1] - fd_a[hlc - 1] : (T)0;
-                            const T Dbd = dn ? fd_a[LW + hlc + 1] - fd_a[LW + hlc - 1] : (T)0;
-                            const T Dau = up ? fu_a[hlc + 1] - fu_a[hlc - 1] : (T)0;
-                            const T Dbu = up ? fu_a[LW + hlc + 1] - fu_a[LW + hlc - 1] : (T)0;
-                            const T* wa = sW + (size_t)sw * 2 * LW;
+                            const T Dad = dn ? fd[hlc + 1] - fd[hlc - 1] : (T)0;
+                            const T Dbd = dn ? fd[LW + hlc + 1] - fd[LW + hlc - 1] : (T)0;
+                            const T Dau = up ? ra[hlc + 1] - ra[hlc - 1] : (T)0;
+                            const T Dbu = up ? ra[LW + hlc + 1] - ra[LW + hlc - 1] : (T)0;
                             cn_cell<T>(wa[hlc], wa[LW + hlc], cc * (Dbu - Dbd), cc * (chi * Dad - Dau),
                                        ha0 * hg, nf * hbs, nf * hbe, nu, xi, h, an, bn);
                             if (j == 0) bn = (T)0;
                         }
-                        T* na = sN + (size_t)(j & 1) * 2 * WN;
-                        const int idx = (lane == 0) ? 1 : Wt + 2;
-                        na[idx] = an;
-                        na[WN + idx] = bn;
+                        na[hidx] = an;
+                        na[WN + hidx] = bn;
                     }
                 }
                 __syncthreads();
                 if (tid == NTr) {
                     /* every stage up to old row j-1 has been read for the last time */
+                    const long long si = j - n0 + 3;
                     const long long f = (j == n1) ? cbase + S : cbase + si - 1;
-                    if (f > freed) freed = f;
+                    if (f > p_freed) p_freed = f;
                     fence_proxy_async_smem();
                     pump();
                 }
 
                 /* ---- new fractional row j-1 ---- */
-                V2 dwa_0 = {0, 0}, dwb_0 = {0, 0};
-                if (wrow && is_comp) {
-                    const T* na = sN + (size_t)(j & 1) * 2 * WN;
-                    const V2 la = *reinterpret_cast<const V2*>(na + 2 * tid);
-                    const V2 pa = *reinterpret_cast<const V2*>(na + 2 * tid + 4);
-                    const V2 lb = *reinterpret_cast<const V2*>(na + WN + 2 * tid);
-                    const V2 pb = *reinterpret_cast<const V2*>(na + WN + 2 * tid + 4);
-                    dwa_0.x = wa_n.y - la.y;
-                    dwa_0.y = pa.x - wa_n.x;
-                    dwb_0.x = wb_n.y - lb.y;
-                    dwb_0.y = pb.x - wb_n.x;
+                T dwa_0[V], dwb_0[V];
+                if (wrow_ok && is_comp) {
+                    T l, r;
+                    neighbours<T, V>(na + ln, l, r);
+                    diffs<T, V>(wa_n, l, r, dwa_0);
+                    neighbours<T, V>(na + WN + ln, l, r);
+                    diffs<T, V>(wb_n, l, r, dwb_0);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < V; ++e) dwa_0[e] = dwb_0[e] = (T)0;
                 }
                 const int r = j - 1;
-                if (r >= n0 && r < n1 && is_comp && ok0) {
+                if (r >= n0 && r < n1 && is_comp && ok[0]) {
                     const T nf = (T)r;
                     const T chi = (r == 1) ? (T)2 : (T)1;
                     const T ha0 = h * sR[r - n0 + 1];
-                    V2 fa_n, fb_n;
-                    cn_cell<T>(fa_m1.x, fb_m1.x, cc * (dwb_0.x - dwb_m2.x),
-                               cc * (chi * dwa_m2.x - dwa_0.x), ha0 * g0, nf * fs0, nf * fe0, nu,
-                               xi, h, fa_n.x, fb_n.x);
-                    cn_cell<T>(fa_m1.y, fb_m1.y, cc * (dwb_0.y - dwb_m2.y),
-                               cc * (chi * dwa_m2.y - dwa_0.y), ha0 * g1, nf * fs1, nf * fe1, nu,
-                               xi, h, fa_n.y, fb_n.y);
-                    if (r == 0) {
-                        fb_n.x = (T)0;
-                        fb_n.y = (T)0;
+                    T fa_n[V], fb_n[V];
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        cn_cell<T>(fa_m1[e], fb_m1[e], cc * (dwb_0[e] - dwb_m2[e]),
+                                   cc * (chi * dwa_m2[e] - dwa_0[e]), ha0 * g[e], nf * fs[e],
+                                   nf * fe[e], nu, xi, h, fa_n[e], fb_n[e]);
+                        if (r == 0) fb_n[e] = (T)0;
                     }
-                    const size_t go = (size_t)r * pitch + c;
-                    if (ok1) {
-                        *reinterpret_cast<V2*>(oFa + go) = fa_n;
-                        *reinterpret_cast<V2*>(oFb + go) = fb_n;
+                    T* frow = oFa + (size_t)r * pitch + c;
+                    if (all_ok) {
+                        st_own<T, V>(frow, fa_n);
+                        st_own<T, V>(frow + dFb, fb_n);
                     } else {
-                        oFa[go] = fa_n.x;
-                        oFb[go] = fb_n.x;
+#pragma unroll
+                        for (int e = 0; e < V; ++e)
+                            if (ok[e]) {
+                                frow[e] = fa_n[e];
+                                frow[dFb + e] = fb_n[e];
+                            }
                     }
                 }
 
@@ -415,19 +475,31 @@ __global__ void __launch_bounds__(MaxBlock<T>::value) fused_step_kernel(StepArgs
                         }
                     }
                 }
-                dwa_m2 = dwa_m1;
-                dwb_m2 = dwb_m1;
-                dwa_m1 = dwa_0;
-                dwb_m1 = dwb_0;
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    dwa_m2[e] = dwa_m1[e];
+                    dwb_m2[e] = dwb_m1[e];
+                    dwa_m1[e] = dwa_0[e];
+                    dwb_m1[e] = dwb_0[e];
+                }
             }
-            fa_m1 = fa_0;
-            fb_m1 = fb_0;
-            fa_0 = fa_p1;
-            fb_0 = fb_p1;
-            dfa_m1 = dfa_0;
-            dfb_m1 = dfb_0;
-            dfa_0 = dfa_p1;
-            dfb_0 = dfb_p1;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                fa_m1[e] = fa_0[e];
+                fb_m1[e] = fb_0[e];
+                fa_0[e] = fa_p1[e];
+                fb_0[e] = fb_p1[e];
+                dfa_m1[e] = dfa_0[e];
+                dfb_m1[e] = dfb_0[e];
+                dfa_0[e] = dfa_p1[e];
+                dfb_0[e] = dfb_p1[e];
+            }
+            slot_m2 = slot_m1;
+            slot_m1 = c_slot;
+            if (++c_slot == RS) {
+                c_slot = 0;
+                c_phase ^= 1u;
+            }
         }
         cbase += S;
     }
@@ -439,48 +511,78 @@ __global__ void __launch_bounds__(MaxBlock<T>::value) fused_step_kernel(StepArgs
 static int ok_or(cudaError_t e) { return e == cudaSuccess ? 0 : (int)e; }
 
 template <typename T>
-size_t step_smem_bytes(int tile_m, int chunk_n) {
+size_t step_smem_bytes(int tile_m, int chunk_n, int vec) {
     size_t a, b, c, d;
-    return smem_layout<T>(tile_m, chunk_n, &a, &b, &c, &d);
+    return smem_layout<T>(tile_m, chunk_n, vec, &a, &b, &c, &d);
 }
 
 template <typename T>
-int step_block_threads(int tile_m) {
-    return round_warp(compute_threads<T>(tile_m)) + 32;
+int step_block_threads(int tile_m, int vec) {
+    return round_warp(tile_m / vec) + 32;
 }
 
 template <typename T>
-int step_max_tile() {
-    return 2 * (MaxBlock<T>::value - 32);
+int step_max_tile(int vec) {
+    if (sizeof(T) == 4 && vec == 2) return 2 * (MaxBlock<float, 2>::value - 32);
+    if (sizeof(T) == 4) return 4 * (MaxBlock<float, 4>::value - 32);
+    return 2 * (MaxBlock<double, 2>::value - 32);
 }
 
 template <typename T>
-int step_kernel_configure(int tile_m, int chunk_n, int* blocks_per_sm) {
-    const size_t bytes = step_smem_bytes<T>(tile_m, chunk_n);
-    cudaError_t e = cudaFuncSetAttribute(fused_step_kernel<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+static const void* step_fn(int vec) {
+    if constexpr (sizeof(T) == 4)
+        return vec == 4 ? reinterpret_cast<const void*>(&fused_step_kernel<float, 4>)
+                        : reinterpret_cast<const void*>(&fused_step_kernel<float, 2>);
+    else
+        return reinterpret_cast<const void*>(&fused_step_kernel<double, 2>);
+}
+
+template <typename T>
+int step_kernel_configure(int tile_m, int chunk_n, int vec, int* blocks_per_sm) {
+    const size_t bytes = step_smem_bytes<T>(tile_m, chunk_n, vec);
+    const void* fn = step_fn<T>(vec);
+    cudaError_t e =
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fused_step_kernel<T>,
-                                                      step_block_threads<T>(tile_m), bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, step_block_threads<T>(tile_m, vec),
+                                                      bytes);
     if (e != cudaSuccess) return (int)e;
     *blocks_per_sm = nb;
     return 0;
 }
 
 template <typename T>
-int launch_step(const StepArgs<T>& a, int i, void* stream) {
-    fused_step_kernel<T><<<a.grid, step_block_threads<T>(a.tile_m),
-                           step_smem_bytes<T>(a.tile_m, a.chunk_n), (cudaStream_t)stream>>>(a, i);
+int launch_step(const StepArgs<T>& a, int i, int parity, bool pdl, void* stream) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.grid);
+    cfg.blockDim = dim3(step_block_threads<T>(a.tile_m, a.vec));
+    cfg.dynamicSmemBytes = step_smem_bytes<T>(a.tile_m, a.chunk_n, a.vec);
+    cfg.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    if constexpr (sizeof(T) == 4) {
+        if (a.vec == 4)
+            e = cudaLaunchKernelEx(&cfg, fused_step_kernel<float, 4>, a, i, parity);
+        else
+            e = cudaLaunchKernelEx(&cfg, fused_step_kernel<float, 2>, a, i, parity);
+    } else {
+        e = cudaLaunchKernelEx(&cfg, fused_step_kernel<double, 2>, a, i, parity);
+    }
+    if (e != cudaSuccess) return (int)e;
     return ok_or(cudaGetLastError());
 }
 
 #define BTE_STEP_INSTANTIATE(T)                                 \
-    template size_t step_smem_bytes<T>(int, int);               \
-    template int step_block_threads<T>(int);                    \
-    template int step_max_tile<T>();                            \
-    template int step_kernel_configure<T>(int, int, int*);      \
-    template int launch_step<T>(const StepArgs<T>&, int, void*);
+    template size_t step_smem_bytes<T>(int, int, int);          \
+    template int step_block_threads<T>(int, int);               \
+    template int step_max_tile<T>(int);                         \
+    template int step_kernel_configure<T>(int, int, int, int*); \
+    template int launch_step<T>(const StepArgs<T>&, int, int, bool, void*);
 BTE_STEP_INSTANTIATE(float)
 BTE_STEP_INSTANTIATE(double)
 

@@ -79,8 +79,8 @@ def _rand_params(n_max, m_points, prec, omega=1.3):
 
 
 @pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("prec", [W.FP64, W.FP32_MIXED])
-def test_random_state_parity(shape, prec):
+@pytest.mark.parametrize("prec,vec", [(W.FP64, 2), (W.FP32_MIXED, 2), (W.FP32_MIXED, 4)])
+def test_random_state_parity(shape, prec, vec):
     """Arbitrary (random) state on both grids, 40 steps at B != 0 and
     E_omega != 0, several launch shapes: element-wise parity of all four
     arrays and of the drift-velocity / norm trace."""
@@ -89,7 +89,7 @@ def test_random_state_parity(shape, prec):
     aw, bw, af, bf = W.random_state(p, seed=11 + n_max)
     st = oracle.State(aw.copy(), bw.copy(), af.copy(), bf.copy())
     v_ref, n_ref = oracle.advance(p, st, 0, 40)
-    with bte.Solver(p, tile_m=tile_m, chunk_n=chunk_n, graph_steps=16) as s:
+    with bte.Solver(p, tile_m=tile_m, chunk_n=chunk_n, graph_steps=16, vec=vec) as s:
         s.set_state(0, aw, bw)
         s.set_state(1, af, bf)
         s.step(40)

@@ -25,7 +25,8 @@ def _plans():
 def test_bulk_copies_aligned_and_in_bounds(case):
     p, tile, chunk = case
     elem = 8 if p.precision == W.FP64 else 4
-    H = 16 // elem
+    H = 16 // elem     # halo columns streamed per side (one TMA granule)
+    G = 128 // elem    # zero ghost columns before m = 0
     try:
         s = bte.launch_shape(p, tile, chunk)
     except bte.BteError as e:
@@ -41,9 +42,10 @@ def test_bulk_copies_aligned_and_in_bounds(case):
     LW = Wt + 2 * H
     assert (LW * elem) % 16 == 0
     for tx in range(ntx):
-        p0 = H + tx * Wt
+        p0 = G + tx * Wt
         first = p0 - H
         assert first >= 0 and (first * elem) % 16 == 0
         assert first + LW <= pitch
+        assert (p0 * elem) % 16 == 0  # vector stores of a thread's columns
     # ghost columns: interior columns G..G+M, zero ghosts on both sides
-    assert H >= 2 and H + M1 + 1 <= pitch
+    assert H >= 2 and G + M1 + 1 <= pitch
