@@ -187,6 +187,9 @@ def oracle_sample(p, target_s: float):
 def run_reference(args):
     world, rank, _ = dist_setup()
     p, desc = workload(args.config, args.precision)
+    if args.periods:
+        p = p.replace(periods=args.periods, avg_window=min(p.avg_window, args.periods))
+        desc += f" (run shortened to {args.periods:g} periods)"
     if rank != 0:
         return 0
     import oracle
@@ -229,6 +232,9 @@ def run_ours(args):
     from paper_1401_6047_gb300 import bte
 
     p, desc = workload(args.config, args.precision)
+    if args.periods:
+        p = p.replace(periods=args.periods, avg_window=min(p.avg_window, args.periods))
+        desc += f" (run shortened to {args.periods:g} periods)"
     dt_eff, P, K, Kw = bte.time_grid(p)
     cells = p.cells
     elem = 8 if args.precision == "fp64" else 4
@@ -383,6 +389,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--periods", type=float, default=0.0,
+                    help="shorter run (drive periods) for profiling; 0 = the workload's")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -135,30 +135,38 @@ int pick_tile(const bte_params* p, const bte_tuning* t, int& tile_m, int& chunk_
         if (tile_m % 4 || tile_m < 32 || tile_m > 1024)
             return fail(BTE_EINVAL, "tile_m must be a multiple of 4 in 32..1024");
     } else {
-        /* fewest wasted columns, preferring wider tiles on ties */
-        const int cand[] = {512, 384, 320, 256, 192, 128};
-        int best = 256;
-        double best_cost = 1e30;
-        for (int c : cand) {
-            const int ntx = (M1 + c - 1) / c;
-            const double waste = (double)(ntx * c - M1) / M1;
-            const double halo = 8.0 / c; /* re-read halo columns */
-            const double cost = waste + halo;
-            if (cost < best_cost - 1e-9) {
-                best_cost = cost;
-                best = c;
+        /* whole warps of compute threads per item: w warps cover 32*vec*w
+         * columns; pick w in 2..6 with the fewest warps over the grid's
+         * width (the producer warp of each item counted as half a warp).
+         * Grids of at most 512 columns use one-warp items so that several
+         * SMs share them. */
+        const int per_warp = 32 * vec;
+        if (M1 <= 512) {
+            tile_m = per_warp;
+        } else {
+            double best = 1e30;
+            for (int w = 2; w <= 6; ++w) {
+                const int t = per_warp * w;
+                if (fp64 && t > 512) break;
+                const int ntx = (M1 + t - 1) / t;
+                const double cost = ntx * (w + 0.5);
+                if (cost < best - 1e-9) {
+                    best = cost;
+                    tile_m = t;
+                }
             }
         }
-        tile_m = best;
-        if (M1 < tile_m) tile_m = std::max(32, (M1 + 3) / 4 * 4);
     }
     if (chunk_n) {
         if (chunk_n < 4) return fail(BTE_EINVAL, "chunk_n must be >= 4");
     } else {
+        /* about one item per resident CTA (persistent launch): ~2 CTAs per
+         * SM; at least 4 rows (8 when rows are plenty) */
         const int ntx = (M1 + tile_m - 1) / tile_m;
-        const int want = 4 * 152; /* enough items for a few per SM */
-        chunk_n = 64;
-        while (chunk_n > 8 && (long long)ntx * ((N1 + chunk_n - 1) / chunk_n) < want) chunk_n /= 2;
+        const int slots = 304;
+        const int rows_per = std::max(1, slots / ntx);
+        chunk_n = (N1 + rows_per - 1) / rows_per;
+        chunk_n = std::max(chunk_n, N1 >= 64 ? 8 : 4);
     }
     return BTE_OK;
 }
