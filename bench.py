@@ -72,7 +72,7 @@ def measured_peaks():
 
 
 def kernel_sha() -> str:
-    src = os.path.join(ROOT, "paper_1401_6047_gb300", "csrc", "bte_kernels.cu")
+    src = os.path.join(ROOT, "paper_1401_6047_gb300", "csrc", "bte_step.cu")
     with open(src, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
