@@ -188,6 +188,25 @@ BTE_API int bte_launch_shape(const bte_params* p, const bte_tuning* tune, int32_
                              int32_t* chunk_n, int32_t* pitch, int32_t* grid_x,
                              int32_t* grid_y);
 
+/* Drift velocity and norm (out[0] = pi sqrt(alpha) dphi sum_m b1_row[m],
+ * out[1] = 2 pi sqrt(alpha) dphi sum_m a0_row[m]) of caller-owned DEVICE
+ * rows a0_row (harmonic n = 0 of a) and b1_row (n = 1 of b), m_points
+ * contiguous values each, FP64 when p->precision is BTE_FP64, else FP32;
+ * out is a DEVICE array of 2 doubles.  Queued on `stream`; returns without
+ * waiting.  The paper has no counterpart to this entry point: it exists for
+ * callers that cannot allocate device memory (applications whose device
+ * memory all belongs to their own pool allocator, host paths that cannot
+ * afford the synchronisation an allocation may cause).  It allocates
+ * nothing: its partial sums and arrival ticket live in one fixed array of
+ * the library (16.6 KB per GPU, held until the process exits), so m_points
+ * may be at most 1,048,576 (BTE_EINVAL beyond that, below 3, or for bad
+ * parameters).  Its first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress, with the device current); make that first
+ * call before any stream capture.  Every call shares the array and clears
+ * the ticket before use; calls that overlap on the GPU race. */
+BTE_API int bte_observe_noalloc(const bte_params* p, const void* a0_row, const void* b1_row,
+                                double* out, void* stream);
+
 /* Library version string. */
 BTE_API const char* bte_version(void);
 

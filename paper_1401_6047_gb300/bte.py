@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
             "bte_time_grid": ([P, dp, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                ctypes.POINTER(i64)], ctypes.c_int),
             "bte_version": ([], ctypes.c_char_p),
+            "bte_observe_noalloc": ([P, vp, vp, vp, vp], ctypes.c_int),
             "bte_launch_shape": ([P, T] + [ctypes.POINTER(ctypes.c_int32)] * 5, ctypes.c_int),
         }
         for name, (args, res) in sig.items():
@@ -167,6 +168,15 @@ def launch_shape(p, tile_m=0, chunk_n=0, vec=0) -> dict:
     v = [ctypes.c_int32() for _ in range(5)]
     _check(lib().bte_launch_shape(ctypes.byref(s), ctypes.byref(t), *(ctypes.byref(x) for x in v)))
     return dict(zip(("tile_m", "chunk_n", "pitch", "grid_x", "grid_y"), (x.value for x in v)))
+
+
+def observe_noalloc(p, a0_row_dev: int, b1_row_dev: int, out_dev: int, stream: int = 0) -> None:
+    """Queues bte_observe_noalloc on device pointers (ints): out_dev[0] =
+    drift velocity, out_dev[1] = norm of the given rows; allocates nothing."""
+    s = to_params(p)
+    _check(lib().bte_observe_noalloc(ctypes.byref(s), ctypes.c_void_p(a0_row_dev),
+                                     ctypes.c_void_p(b1_row_dev), ctypes.c_void_p(out_dev),
+                                     ctypes.c_void_p(stream or None)))
 
 
 @dataclass
