@@ -90,6 +90,18 @@ __device__ __forceinline__ double recip<double>(double x) {
     return 1.0 / x;
 }
 
+/* a * b + c with one rounding. */
+template <typename T>
+__device__ __forceinline__ T fma_t(T a, T b, T c);
+template <>
+__device__ __forceinline__ float fma_t<float>(float a, float b, float c) {
+    return fmaf(a, b, c);
+}
+template <>
+__device__ __forceinline__ double fma_t<double>(double a, double b, double c) {
+    return fma(a, b, c);
+}
+
 /* Crank-Nicolson update of one cell (Sec. 3, Eqs. a_t_plus_1, b_t_plus_1,
  * with the sign of b' that solves nu a' + th1 b' = g, -th1 a' + nu b' = q),
  * written as increments so that FP32 keeps the O(h) relaxation balance:

@@ -174,7 +174,7 @@ int pick_tile(const bte_params* p, const bte_tuning* t, int& tile_m, int& chunk_
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-    int G, H, pitch, tile_m, chunk_n, vec, ntx, nty;
+    int G, H, pitch, tile_m, chunk_n, vec, ts, ntx, nty;
     size_t elem;
     size_t off_state[8];
     size_t off_row_a0, off_col_g, off_col_bphi, off_ew, off_ef, off_tv, off_tn, off_part,
@@ -186,15 +186,16 @@ int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L
     if (rc) return rc;
     L.elem = p->precision == BTE_FP64 ? 8 : 4;
     L.G = (int)(128 / L.elem);
-    L.H = (int)(16 / L.elem);
+    L.H = (int)(32 / L.elem); /* halo columns the step kernel streams per side */
     const int max_tile = L.elem == 8 ? bte::step_max_tile<double>(L.vec)
                                      : bte::step_max_tile<float>(L.vec);
     if (L.tile_m > max_tile) {
         if (t && t->tile_m) return fail(BTE_EINVAL, "tile_m %d above %d for this precision", L.tile_m, max_tile);
         L.tile_m = max_tile;
     }
-    const size_t smem = L.elem == 8 ? bte::step_smem_bytes<double>(L.tile_m, L.chunk_n, L.vec)
-                                    : bte::step_smem_bytes<float>(L.tile_m, L.chunk_n, L.vec);
+    L.ts = (L.elem == 4 && L.vec == 4) ? 2 : 1; /* steps fused per launch */
+    const size_t smem = L.elem == 8 ? bte::step_smem_bytes<double>(L.tile_m, L.chunk_n, L.vec, L.ts)
+                                    : bte::step_smem_bytes<float>(L.tile_m, L.chunk_n, L.vec, L.ts);
     if (smem > 227 * 1024)
         return fail(BTE_EINVAL, "tile_m %d needs %zu bytes of shared memory", L.tile_m, smem);
     const int M1 = p->m_points, N1 = p->n_max + 1;
@@ -216,15 +217,15 @@ int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L
     o += align_up((size_t)L.pitch * L.elem, 256);
     const long long Pt = tg.P > 0 ? tg.P : 1;
     L.off_ew = o;
-    o += align_up((size_t)(Pt + 1) * 8, 256);
+    o += align_up((size_t)(Pt + 2) * 8, 256);
     L.off_ef = o;
-    o += align_up((size_t)(Pt + 1) * 8, 256);
+    o += align_up((size_t)(Pt + 2) * 8, 256);
     L.off_tv = o;
     o += align_up((size_t)(tg.K + 1) * 8, 256);
     L.off_tn = o;
     o += align_up((size_t)(tg.K + 1) * 8, 256);
     L.off_part = o;
-    o += align_up((size_t)2 * L.ntx * 8, 256);
+    o += align_up((size_t)2 * L.ts * L.ntx * 8, 256);
     L.off_ticket = o;
     o += 256;
     L.off_err = o;
@@ -251,9 +252,10 @@ struct bte_handle {
     cudaStream_t cap_stream;
     long long k;   /* steps queued so far */
     long long base_host;
-    int graph_len;
-    int grid;      /* persistent CTAs of the step kernel */
-    cudaGraphExec_t graph[2]; /* graph_len steps starting on an even / odd step */
+    int graph_len; /* steps per captured graph (a multiple of the fused step count) */
+    int grid[3];   /* persistent CTAs of the step kernel fusing 1 / 2 steps */
+    int set;       /* ping-pong set holding the current state (flips per launch) */
+    cudaGraphExec_t graph[2]; /* one graph per starting set */
     double r1;     /* I_1/I_0 */
     double dphi;
     template <typename T>
@@ -294,7 +296,7 @@ bte::StepArgs<T> step_args(const bte_handle* h) {
     a.ntx = L.ntx;
     a.nty = L.nty;
     a.vec = L.vec;
-    a.grid = h->grid;
+    a.grid = h->grid[L.ts];
     const double dt = h->tg.dt_eff;
     a.h = (T)dt;
     a.hh = (T)(0.5 * dt);
@@ -324,8 +326,8 @@ int upload_tables(bte_handle* h) {
         colb[L.G + m] = (T)(p.B * phi);
     }
     const long long Pt = h->tg.P > 0 ? h->tg.P : 1;
-    std::vector<double> ew(Pt + 1), ef(Pt + 1);
-    for (long long q = 0; q <= Pt; ++q) {
+    std::vector<double> ew(Pt + 2), ef(Pt + 2);
+    for (long long q = 0; q <= Pt + 1; ++q) {
         if (h->tg.P > 0) {
             ew[q] = p.E_dc + p.E_omega * std::cos(kTwoPi * (double)q / (double)Pt);
             ef[q] = p.E_dc + p.E_omega * std::cos(kTwoPi * ((double)q + 0.5) / (double)Pt);
@@ -339,9 +341,9 @@ int upload_tables(bte_handle* h) {
                        cudaMemcpyHostToDevice, h->stream));
     CU(cudaMemcpyAsync(h->ptr<T>(L.off_col_bphi), colb.data(), L.pitch * sizeof(T),
                        cudaMemcpyHostToDevice, h->stream));
-    CU(cudaMemcpyAsync(h->ptr<double>(L.off_ew), ew.data(), (Pt + 1) * 8, cudaMemcpyHostToDevice,
+    CU(cudaMemcpyAsync(h->ptr<double>(L.off_ew), ew.data(), (Pt + 2) * 8, cudaMemcpyHostToDevice,
                        h->stream));
-    CU(cudaMemcpyAsync(h->ptr<double>(L.off_ef), ef.data(), (Pt + 1) * 8, cudaMemcpyHostToDevice,
+    CU(cudaMemcpyAsync(h->ptr<double>(L.off_ef), ef.data(), (Pt + 2) * 8, cudaMemcpyHostToDevice,
                        h->stream));
     CU(cudaStreamSynchronize(h->stream)); /* host vectors go out of scope */
     return BTE_OK;
@@ -394,20 +396,24 @@ int initialise(bte_handle* h, bool full, bool sync) {
                                 sa.trace_n, 0, h->stream);
     if (rc) return fail(BTE_ECUDA, "observe kernel: %s", cudaGetErrorString((cudaError_t)rc));
     h->k = 0;
+    h->set = 0;
     h->base_host = 0;
     if (sync) CU(cudaStreamSynchronize(h->stream));
     return BTE_OK;
 }
 
 template <typename T>
-int capture_graph(bte_handle* h, int parity) {
-    const bte::StepArgs<T> a = step_args<T>(h);
+int capture_graph(bte_handle* h, int set) {
+    bte::StepArgs<T> a = step_args<T>(h);
+    const int ts = h->L.ts;
+    a.grid = h->grid[ts];
     long long* base = h->ptr<long long>(h->L.off_base);
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = 0;
-    for (int i = 0; i < h->graph_len && !rc; ++i)
-        rc = bte::launch_step<T>(a, i, parity, i > 0, h->cap_stream);
+    const int launches = h->graph_len / ts;
+    for (int i = 0; i < launches && !rc; ++i)
+        rc = bte::launch_step<T>(a, ts, i, set, i > 0, h->cap_stream);
     if (!rc) rc = bte::launch_advance_base(base, h->graph_len, h->cap_stream);
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
     if (rc || e != cudaSuccess) {
@@ -415,40 +421,58 @@ int capture_graph(bte_handle* h, int parity) {
         return fail(BTE_ECUDA, "graph capture failed: %s",
                     cudaGetErrorString(e != cudaSuccess ? e : (cudaError_t)rc));
     }
-    e = cudaGraphInstantiate(&h->graph[parity], g, 0);
+    e = cudaGraphInstantiate(&h->graph[set], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        h->graph[parity] = nullptr;
+        h->graph[set] = nullptr;
         return fail(BTE_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
     }
     return BTE_OK;
 }
 
-/* Queues n steps: whole graphs of graph_len steps (one per parity of the
- * first step, captured on first use), then single launches.  Launches after
- * the first of a run use programmatic dependent launch. */
+/* Queues n steps: whole graphs of graph_len steps (one graph per starting
+ * ping-pong set, captured on first use), then single launches fusing ts
+ * steps and, for an odd remainder, one single-step launch.  Every launch
+ * flips the ping-pong set; launches after the first of a run use
+ * programmatic dependent launch. */
 template <typename T>
 int enqueue_steps(bte_handle* h, long long n) {
-    while (h->graph_len > 1 && n >= h->graph_len) {
-        const int par = (int)(h->k & 1);
-        if (!h->graph[par]) {
-            int rc = capture_graph<T>(h, par);
+    const int ts = h->L.ts;
+    while (h->graph_len >= 2 * ts && n >= h->graph_len) {
+        const int set = h->set;
+        if (!h->graph[set]) {
+            int rc = capture_graph<T>(h, set);
             if (rc) return rc;
         }
-        CU(cudaGraphLaunch(h->graph[par], h->stream));
+        CU(cudaGraphLaunch(h->graph[set], h->stream));
         n -= h->graph_len;
         h->k += h->graph_len;
+        h->set ^= (h->graph_len / ts) & 1;
     }
     if (n > 0) {
-        const bte::StepArgs<T> a = step_args<T>(h);
-        const int par = (int)(h->k & 1);
-        for (long long i = 0; i < n; ++i) {
-            int rc = bte::launch_step<T>(a, (int)i, par, i > 0, h->stream);
-            if (rc) return fail(BTE_ECUDA, "step kernel: %s", cudaGetErrorString((cudaError_t)rc));
+        bte::StepArgs<T> a = step_args<T>(h);
+        const int set = h->set;
+        int i = 0;
+        long long left = n;
+        int rc = 0;
+        for (; left >= ts && !rc; left -= ts, ++i) {
+            a.grid = h->grid[ts];
+            rc = bte::launch_step<T>(a, ts, i, set, i > 0, h->stream);
         }
-        int rc = bte::launch_advance_base(h->ptr<long long>(h->L.off_base), n, h->stream);
-        if (rc) return fail(BTE_ECUDA, "counter kernel: %s", cudaGetErrorString((cudaError_t)rc));
+        /* single steps after fused ones advance from step base + i*ts; the
+         * kernel reads base + launch_i * TS, so the remainder is queued after
+         * the counter has moved */
+        if (!rc && i > 0) rc = bte::launch_advance_base(h->ptr<long long>(h->L.off_base), (long long)i * ts, h->stream);
+        int set2 = set ^ (i & 1);
+        int i2 = 0;
+        for (; left > 0 && !rc; --left, ++i2) {
+            a.grid = h->grid[1];
+            rc = bte::launch_step<T>(a, 1, i2, set2, i2 > 0, h->stream);
+        }
+        if (!rc && i2 > 0) rc = bte::launch_advance_base(h->ptr<long long>(h->L.off_base), i2, h->stream);
+        if (rc) return fail(BTE_ECUDA, "step kernel: %s", cudaGetErrorString((cudaError_t)rc));
         h->k += n;
+        h->set = set2 ^ (i2 & 1);
     }
     return BTE_OK;
 }
@@ -456,7 +480,7 @@ int enqueue_steps(bte_handle* h, long long n) {
 template <typename T>
 int get_grid(bte_handle* h, int grid, double* a, double* b) {
     const Layout& L = h->L;
-    const int set = (int)(h->k & 1);
+    const int set = h->set;
     const int N1 = h->p.n_max + 1, M1 = h->p.m_points;
     const T* da = h->ptr<T>(L.off_state[4 * set + 2 * grid + 0]);
     const T* db = h->ptr<T>(L.off_state[4 * set + 2 * grid + 1]);
@@ -476,7 +500,7 @@ int get_grid(bte_handle* h, int grid, double* a, double* b) {
 template <typename T>
 int set_grid(bte_handle* h, int grid, const double* a, const double* b) {
     const Layout& L = h->L;
-    const int set = (int)(h->k & 1);
+    const int set = h->set;
     const int N1 = h->p.n_max + 1, M1 = h->p.m_points;
     for (int m = 0; m < M1; ++m)
         if (b[m] != 0.0) return fail(BTE_EINVAL, "b[0][*] must be 0 (Eq. b_boundary)");
@@ -571,6 +595,7 @@ int bte_create_ex(const bte_params* p, void* stream, const bte_tuning* tune, voi
     }
     h->graph_len = (tune && tune->graph_steps > 0) ? tune->graph_steps : 1024;
     if (h->graph_len > h->tg.K) h->graph_len = (int)h->tg.K;
+    h->graph_len -= h->graph_len % h->L.ts; /* whole fused launches per graph */
     auto bail = [&](int code) {
         bte_destroy(h);
         return code;
@@ -609,16 +634,18 @@ int bte_create_ex(const bte_params* p, void* stream, const bte_tuning* tune, voi
     }
     {
         int bps = 0, dev = 0, sms = 0;
-        rc = h->fp64 ? bte::step_kernel_configure<double>(h->L.tile_m, h->L.chunk_n, h->L.vec, &bps)
-                     : bte::step_kernel_configure<float>(h->L.tile_m, h->L.chunk_n, h->L.vec, &bps);
-        if (rc)
-            return bail(fail(BTE_ECUDA, "kernel configure: %s", cudaGetErrorString((cudaError_t)rc)));
-        if (bps < 1) return bail(fail(BTE_EINVAL, "launch shape does not fit on an SM"));
         CU(cudaGetDevice(&dev));
         CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         const long long items = (long long)h->L.ntx * h->L.nty;
-        const long long slots = (long long)bps * sms;
-        h->grid = (int)(items < slots ? items : slots);
+        for (int ts = 1; ts <= h->L.ts; ++ts) {
+            rc = h->fp64 ? bte::step_kernel_configure<double>(h->L.tile_m, h->L.chunk_n, h->L.vec, ts, &bps)
+                         : bte::step_kernel_configure<float>(h->L.tile_m, h->L.chunk_n, h->L.vec, ts, &bps);
+            if (rc)
+                return bail(fail(BTE_ECUDA, "kernel configure: %s", cudaGetErrorString((cudaError_t)rc)));
+            if (bps < 1) return bail(fail(BTE_EINVAL, "launch shape does not fit on an SM"));
+            const long long slots = (long long)bps * sms;
+            h->grid[ts] = (int)(items < slots ? items : slots);
+        }
     }
     rc = h->fp64 ? upload_tables<double>(h) : upload_tables<float>(h);
     if (rc) return bail(rc);
@@ -727,15 +754,6 @@ int bte_set_state(bte_handle* h, int grid, const double* a, const double* b) {
 int bte_set_step(bte_handle* h, int64_t k, const double* v, const double* norm) {
     if (!h || !v || !norm) return fail(BTE_EINVAL, "bad argument");
     if (k < 0 || k > h->tg.K) return fail(BTE_EINVAL, "step %lld outside 0..%lld", (long long)k, h->tg.K);
-    /* the state of step k must sit in ping-pong set (k & 1): move it if the
-     * parity changes */
-    if ((k & 1) != (h->k & 1)) {
-        const Layout& L = h->L;
-        const int from = (int)(h->k & 1), to = from ^ 1;
-        for (int q = 0; q < 4; ++q)
-            CU(cudaMemcpyAsync(h->mem + L.off_state[4 * to + q], h->mem + L.off_state[4 * from + q],
-                               L.off_state[1] - L.off_state[0], cudaMemcpyDeviceToDevice, h->stream));
-    }
     h->base_host = k;
     CU(cudaMemcpyAsync(h->ptr<long long>(h->L.off_base), &h->base_host, 8, cudaMemcpyHostToDevice,
                        h->stream));

@@ -22,12 +22,12 @@ namespace bte {
 constexpr int kErrTimeout = 1;
 
 /* Column layout constants: G zero ghost columns before m = 0 (128 bytes),
- * H halo columns streamed on each side of a tile (16 bytes, the TMA
- * granule). */
+ * H halo columns streamed on each side of a tile (32 bytes: one column
+ * group of up to 4 values plus its neighbour, rounded to TMA granules). */
 template <typename T>
 struct Cols {
     static constexpr int G = 128 / (int)sizeof(T);
-    static constexpr int H = 16 / (int)sizeof(T);
+    static constexpr int H = 32 / (int)sizeof(T);
 };
 
 /* Arguments of the fused step kernel (one leap-frog step). */
@@ -40,12 +40,12 @@ struct StepArgs {
     const T* row_a0;      /* [N+1]   sigma_n I_n/I_0 / pi                        */
     const T* col_g;       /* [pitch] sqrt(mu/(2 pi alpha)) exp(-mu phi^2/2), 0 in ghosts */
     const T* col_bphi;    /* [pitch] B phi_y(m), 0 in ghosts                    */
-    const double* e_whole;/* [P+1]   E(i dt_eff)                                 */
-    const double* e_frac; /* [P+1]   E((i + 1/2) dt_eff)                         */
+    const double* e_whole;/* [P+2]   E(i dt_eff)                                 */
+    const double* e_frac; /* [P+2]   E((i + 1/2) dt_eff)                         */
     const long long* base;/* device step counter: the launch advances step base+i */
     double* trace_v;      /* [K+1] whole-grid v_dr samples                       */
     double* trace_n;      /* [K+1] whole-grid norm samples                       */
-    double* part;         /* [2][ntx] per-tile partial sums of row 0 / row 1     */
+    double* part;         /* [ts][2][ntx] per-tile partial sums of row 0 / row 1 */
     unsigned* ticket;     /* arrival counter of the row-0 CTAs                   */
     int* err;             /* device error word (timeouts)                        */
     int N, M, pitch, P;
@@ -83,11 +83,12 @@ int launch_init(T* a_w, T* b_w, const T* row_a0, const T* col_g, int N, int M, i
                 void* stream);
 template <typename T>
 int launch_apply(const ApplyArgs<T>& a, void* stream);
-/* Launches step base+i; `parity` = (base & 1) as known to the host, so the
- * ping-pong set is chosen without a device read.  `pdl` enables
- * programmatic dependent launch (the prologue overlaps the previous step). */
+/* Launches ts (1 or 2) fused steps starting at step base + i*ts, reading
+ * ping-pong set (parity + i) & 1 and writing the other one (the host knows
+ * the set, so no device read is needed to choose it).  `pdl` enables
+ * programmatic dependent launch (the prologue overlaps the previous launch). */
 template <typename T>
-int launch_step(const StepArgs<T>& a, int i, int parity, bool pdl, void* stream);
+int launch_step(const StepArgs<T>& a, int ts, int i, int parity, bool pdl, void* stream);
 template <typename T>
 int launch_observe(const T* a_w, const T* b_w, int M, int pitch, double vscale,
                    double nscale, double* trace_v, double* trace_n, long long slot,
@@ -95,12 +96,12 @@ int launch_observe(const T* a_w, const T* b_w, int M, int pitch, double vscale,
 int launch_advance_base(long long* base, long long by, void* stream);
 int launch_finalize(const FinalArgs& a, void* stream);
 template <typename T>
-size_t step_smem_bytes(int tile_m, int chunk_n, int vec);
+size_t step_smem_bytes(int tile_m, int chunk_n, int vec, int ts);
 template <typename T>
 int step_block_threads(int tile_m, int vec);
 template <typename T>
 int step_max_tile(int vec);
 template <typename T>
-int step_kernel_configure(int tile_m, int chunk_n, int vec, int* blocks_per_sm);
+int step_kernel_configure(int tile_m, int chunk_n, int vec, int ts, int* blocks_per_sm);
 
 }  // namespace bte
