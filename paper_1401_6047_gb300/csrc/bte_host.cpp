@@ -193,9 +193,9 @@ int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L
         if (t && t->tile_m) return fail(BTE_EINVAL, "tile_m %d above %d for this precision", L.tile_m, max_tile);
         L.tile_m = max_tile;
     }
-    L.ts = (L.elem == 4 && L.vec == 4) ? 2 : 1; /* steps fused per launch */
-    const size_t smem = L.elem == 8 ? bte::step_smem_bytes<double>(L.tile_m, L.chunk_n, L.vec, L.ts)
-                                    : bte::step_smem_bytes<float>(L.tile_m, L.chunk_n, L.vec, L.ts);
+    L.ts = 1; /* steps per launch */
+    const size_t smem = L.elem == 8 ? bte::step_smem_bytes<double>(L.tile_m, L.chunk_n, L.vec)
+                                    : bte::step_smem_bytes<float>(L.tile_m, L.chunk_n, L.vec);
     if (smem > 227 * 1024)
         return fail(BTE_EINVAL, "tile_m %d needs %zu bytes of shared memory", L.tile_m, smem);
     const int M1 = p->m_points, N1 = p->n_max + 1;
@@ -404,16 +404,13 @@ int initialise(bte_handle* h, bool full, bool sync) {
 
 template <typename T>
 int capture_graph(bte_handle* h, int set) {
-    bte::StepArgs<T> a = step_args<T>(h);
-    const int ts = h->L.ts;
-    a.grid = h->grid[ts];
+    const bte::StepArgs<T> a = step_args<T>(h);
     long long* base = h->ptr<long long>(h->L.off_base);
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = 0;
-    const int launches = h->graph_len / ts;
-    for (int i = 0; i < launches && !rc; ++i)
-        rc = bte::launch_step<T>(a, ts, i, set, i > 0, h->cap_stream);
+    for (int i = 0; i < h->graph_len && !rc; ++i)
+        rc = bte::launch_step<T>(a, i, set, i > 0, h->cap_stream);
     if (!rc) rc = bte::launch_advance_base(base, h->graph_len, h->cap_stream);
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
     if (rc || e != cudaSuccess) {
@@ -431,14 +428,12 @@ int capture_graph(bte_handle* h, int set) {
 }
 
 /* Queues n steps: whole graphs of graph_len steps (one graph per starting
- * ping-pong set, captured on first use), then single launches fusing ts
- * steps and, for an odd remainder, one single-step launch.  Every launch
- * flips the ping-pong set; launches after the first of a run use
- * programmatic dependent launch. */
+ * ping-pong set, captured on first use), then single launches.  Every launch
+ * advances one step and flips the ping-pong set; launches after the first of
+ * a run use programmatic dependent launch. */
 template <typename T>
 int enqueue_steps(bte_handle* h, long long n) {
-    const int ts = h->L.ts;
-    while (h->graph_len >= 2 * ts && n >= h->graph_len) {
+    while (h->graph_len >= 2 && n >= h->graph_len) {
         const int set = h->set;
         if (!h->graph[set]) {
             int rc = capture_graph<T>(h, set);
@@ -447,32 +442,18 @@ int enqueue_steps(bte_handle* h, long long n) {
         CU(cudaGraphLaunch(h->graph[set], h->stream));
         n -= h->graph_len;
         h->k += h->graph_len;
-        h->set ^= (h->graph_len / ts) & 1;
+        h->set ^= h->graph_len & 1;
     }
     if (n > 0) {
-        bte::StepArgs<T> a = step_args<T>(h);
+        const bte::StepArgs<T> a = step_args<T>(h);
         const int set = h->set;
-        int i = 0;
-        long long left = n;
         int rc = 0;
-        for (; left >= ts && !rc; left -= ts, ++i) {
-            a.grid = h->grid[ts];
-            rc = bte::launch_step<T>(a, ts, i, set, i > 0, h->stream);
-        }
-        /* single steps after fused ones advance from step base + i*ts; the
-         * kernel reads base + launch_i * TS, so the remainder is queued after
-         * the counter has moved */
-        if (!rc && i > 0) rc = bte::launch_advance_base(h->ptr<long long>(h->L.off_base), (long long)i * ts, h->stream);
-        int set2 = set ^ (i & 1);
-        int i2 = 0;
-        for (; left > 0 && !rc; --left, ++i2) {
-            a.grid = h->grid[1];
-            rc = bte::launch_step<T>(a, 1, i2, set2, i2 > 0, h->stream);
-        }
-        if (!rc && i2 > 0) rc = bte::launch_advance_base(h->ptr<long long>(h->L.off_base), i2, h->stream);
+        for (long long i = 0; i < n && !rc; ++i)
+            rc = bte::launch_step<T>(a, (int)i, set, i > 0, h->stream);
+        if (!rc) rc = bte::launch_advance_base(h->ptr<long long>(h->L.off_base), n, h->stream);
         if (rc) return fail(BTE_ECUDA, "step kernel: %s", cudaGetErrorString((cudaError_t)rc));
         h->k += n;
-        h->set = set2 ^ (i2 & 1);
+        h->set ^= (int)(n & 1);
     }
     return BTE_OK;
 }
@@ -595,7 +576,6 @@ int bte_create_ex(const bte_params* p, void* stream, const bte_tuning* tune, voi
     }
     h->graph_len = (tune && tune->graph_steps > 0) ? tune->graph_steps : 1024;
     if (h->graph_len > h->tg.K) h->graph_len = (int)h->tg.K;
-    h->graph_len -= h->graph_len % h->L.ts; /* whole fused launches per graph */
     auto bail = [&](int code) {
         bte_destroy(h);
         return code;
@@ -634,18 +614,17 @@ int bte_create_ex(const bte_params* p, void* stream, const bte_tuning* tune, voi
     }
     {
         int bps = 0, dev = 0, sms = 0;
-        CU(cudaGetDevice(&dev));
-        CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return bail(fail(BTE_ECUDA, "no CUDA device"));
         const long long items = (long long)h->L.ntx * h->L.nty;
-        for (int ts = 1; ts <= h->L.ts; ++ts) {
-            rc = h->fp64 ? bte::step_kernel_configure<double>(h->L.tile_m, h->L.chunk_n, h->L.vec, ts, &bps)
-                         : bte::step_kernel_configure<float>(h->L.tile_m, h->L.chunk_n, h->L.vec, ts, &bps);
-            if (rc)
-                return bail(fail(BTE_ECUDA, "kernel configure: %s", cudaGetErrorString((cudaError_t)rc)));
-            if (bps < 1) return bail(fail(BTE_EINVAL, "launch shape does not fit on an SM"));
-            const long long slots = (long long)bps * sms;
-            h->grid[ts] = (int)(items < slots ? items : slots);
-        }
+        rc = h->fp64 ? bte::step_kernel_configure<double>(h->L.tile_m, h->L.chunk_n, h->L.vec, &bps)
+                     : bte::step_kernel_configure<float>(h->L.tile_m, h->L.chunk_n, h->L.vec, &bps);
+        if (rc)
+            return bail(fail(BTE_ECUDA, "kernel configure: %s", cudaGetErrorString((cudaError_t)rc)));
+        if (bps < 1) return bail(fail(BTE_EINVAL, "launch shape does not fit on an SM"));
+        const long long slots = (long long)bps * sms;
+        h->grid[1] = (int)(items < slots ? items : slots);
     }
     rc = h->fp64 ? upload_tables<double>(h) : upload_tables<float>(h);
     if (rc) return bail(rc);

@@ -22,12 +22,12 @@ namespace bte {
 constexpr int kErrTimeout = 1;
 
 /* Column layout constants: G zero ghost columns before m = 0 (128 bytes),
- * H halo columns streamed on each side of a tile (32 bytes: one column
- * group of up to 4 values plus its neighbour, rounded to TMA granules). */
+ * H halo columns streamed on each side of a tile (16 bytes, the TMA
+ * granule; the row pitch leaves room for 32). */
 template <typename T>
 struct Cols {
     static constexpr int G = 128 / (int)sizeof(T);
-    static constexpr int H = 32 / (int)sizeof(T);
+    static constexpr int H = 16 / (int)sizeof(T);
 };
 
 /* Arguments of the fused step kernel (one leap-frog step). */
@@ -83,12 +83,12 @@ int launch_init(T* a_w, T* b_w, const T* row_a0, const T* col_g, int N, int M, i
                 void* stream);
 template <typename T>
 int launch_apply(const ApplyArgs<T>& a, void* stream);
-/* Launches ts (1 or 2) fused steps starting at step base + i*ts, reading
- * ping-pong set (parity + i) & 1 and writing the other one (the host knows
- * the set, so no device read is needed to choose it).  `pdl` enables
- * programmatic dependent launch (the prologue overlaps the previous launch). */
+/* Launches step base + i, reading ping-pong set (parity + i) & 1 and writing
+ * the other one (the host knows the set, so no device read is needed to
+ * choose it).  `pdl` enables programmatic dependent launch (the prologue
+ * overlaps the previous launch). */
 template <typename T>
-int launch_step(const StepArgs<T>& a, int ts, int i, int parity, bool pdl, void* stream);
+int launch_step(const StepArgs<T>& a, int i, int parity, bool pdl, void* stream);
 template <typename T>
 int launch_observe(const T* a_w, const T* b_w, int M, int pitch, double vscale,
                    double nscale, double* trace_v, double* trace_n, long long slot,
@@ -96,12 +96,12 @@ int launch_observe(const T* a_w, const T* b_w, int M, int pitch, double vscale,
 int launch_advance_base(long long* base, long long by, void* stream);
 int launch_finalize(const FinalArgs& a, void* stream);
 template <typename T>
-size_t step_smem_bytes(int tile_m, int chunk_n, int vec, int ts);
+size_t step_smem_bytes(int tile_m, int chunk_n, int vec);
 template <typename T>
 int step_block_threads(int tile_m, int vec);
 template <typename T>
 int step_max_tile(int vec);
 template <typename T>
-int step_kernel_configure(int tile_m, int chunk_n, int vec, int ts, int* blocks_per_sm);
+int step_kernel_configure(int tile_m, int chunk_n, int vec, int* blocks_per_sm);
 
 }  // namespace bte
