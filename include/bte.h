@@ -207,6 +207,37 @@ BTE_API int bte_launch_shape(const bte_params* p, const bte_tuning* tune, int32_
 BTE_API int bte_observe_noalloc(const bte_params* p, const void* a0_row, const void* b1_row,
                                 double* out, void* stream);
 
+/* Options of bte_batch_run (zero fields take the defaults given). */
+typedef struct bte_batch_opts {
+    int32_t tile_m;          /* phi_y columns per work item (0: 32 * vec)             */
+    int32_t chunk_n;         /* harmonics per work item (0: 16)                       */
+    int32_t vec;             /* columns per thread, 2 or 4 (0: 4 FP32, 2 FP64)        */
+    int32_t graph_steps;     /* steps per captured CUDA graph (0: 1024)               */
+    int32_t max_batch;       /* parameter points advanced together (0: 1024)          */
+    int32_t reserved;
+    int64_t max_batch_bytes; /* device bytes one batch may hold (0: 4 GiB)            */
+    void* stream;            /* cudaStream_t to queue on (NULL: a private stream)     */
+} bte_batch_opts;
+
+/* Full solve (Sec. 3 scheme from the Sec. 2 initial state, window averages
+ * of Eq. absorption_def) of n independent parameter points p[0..n-1], as a
+ * parameter sweep of the kind behind the paper's absorption and drift maps
+ * (Sec. 4).  All points must share one precision; each keeps its own grid,
+ * time step and run length.  Points are grouped into batches (longest runs
+ * first, at most max_batch points and about max_batch_bytes of device
+ * memory each); the points of a batch advance in lock-step, one fused
+ * launch per time step covering every point's tiles, so a batch of small
+ * grids fills the GPU where one small grid cannot.  A point whose run is
+ * over is skipped by later launches of its batch.  out[i] receives the
+ * final observables of p[i] exactly as bte_observables reports them after
+ * bte_run (absorption NaN when omega == 0), with a per-point status
+ * (BTE_OK, BTE_EUNSTABLE, BTE_ETIMEOUT).  Returns BTE_OK when every point
+ * is OK, else the worst status; BTE_EINVAL (nothing run) for a bad point or
+ * option, BTE_ENOMEM / BTE_ECUDA when device work fails (later points are
+ * not run).  Blocks until done; allocates and frees its device memory. */
+BTE_API int bte_batch_run(const bte_params* p, int32_t n, bte_obs* out,
+                          const bte_batch_opts* opts);
+
 /* Library version string. */
 BTE_API const char* bte_version(void);
 

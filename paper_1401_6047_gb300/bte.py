@@ -54,6 +54,13 @@ class bte_tuning(ctypes.Structure):
                 ("graph_steps", ctypes.c_int32), ("vec", ctypes.c_int32)]
 
 
+class bte_batch_opts(ctypes.Structure):
+    _fields_ = [("tile_m", ctypes.c_int32), ("chunk_n", ctypes.c_int32), ("vec", ctypes.c_int32),
+                ("graph_steps", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("max_batch_bytes", ctypes.c_int64),
+                ("stream", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -93,6 +100,8 @@ def lib() -> ctypes.CDLL:
             "bte_version": ([], ctypes.c_char_p),
             "bte_observe_noalloc": ([P, vp, vp, vp, vp], ctypes.c_int),
             "bte_launch_shape": ([P, T] + [ctypes.POINTER(ctypes.c_int32)] * 5, ctypes.c_int),
+            "bte_batch_run": ([P, ctypes.c_int32, ctypes.POINTER(bte_obs),
+                               ctypes.POINTER(bte_batch_opts)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -247,9 +256,7 @@ class Solver:
         rc = self._lib.bte_observables(self._h, ctypes.byref(o))
         if check:
             _check(rc)
-        return Observables(o.t, o.step, o.v_dr, o.norm, o.v_dc_avg, o.absorption,
-                           o.norm_max_abs_err, o.dt_eff, o.steps_total, o.steps_per_period,
-                           o.window_steps, o.status)
+        return _obs(o)
 
     def trace(self, k0: int = 0, count: int | None = None):
         if count is None:
@@ -276,6 +283,34 @@ class Solver:
         norm = np.ascontiguousarray(norm, dtype=np.float64)
         assert len(v) >= k + 1 and len(norm) >= k + 1
         _check(self._lib.bte_set_step(self._h, int(k), _dp(v), _dp(norm)))
+
+
+def _obs(o: bte_obs) -> Observables:
+    return Observables(o.t, o.step, o.v_dr, o.norm, o.v_dc_avg, o.absorption,
+                       o.norm_max_abs_err, o.dt_eff, o.steps_total, o.steps_per_period,
+                       o.window_steps, o.status)
+
+
+def batch_run(points, tile_m: int = 0, chunk_n: int = 0, vec: int = 0, graph_steps: int = 0,
+              max_batch: int = 0, max_batch_bytes: int = 0, stream: int = 0,
+              check: bool = True) -> list[Observables]:
+    """Full solves of many parameter points (``bte_batch_run``); returns one
+    ``Observables`` per point, in order.  With ``check`` a non-OK overall
+    status raises; without it the per-point ``status`` fields tell."""
+    pts = list(points)
+    n = len(pts)
+    arr = (bte_params * max(n, 1))(*[to_params(q) for q in pts])
+    out = (bte_obs * max(n, 1))()
+    o = bte_batch_opts()
+    o.tile_m, o.chunk_n, o.vec, o.graph_steps = int(tile_m), int(chunk_n), int(vec), int(graph_steps)
+    o.max_batch, o.reserved, o.max_batch_bytes = int(max_batch), 0, int(max_batch_bytes)
+    o.stream = ctypes.c_void_p(stream or None)
+    rc = lib().bte_batch_run(arr, n, out, ctypes.byref(o))
+    if check:
+        _check(rc)
+    elif rc in (EINVAL, ENOMEM, ECUDA):
+        _check(rc)
+    return [_obs(out[i]) for i in range(n)]
 
 
 def solve(p, **kw) -> Observables:

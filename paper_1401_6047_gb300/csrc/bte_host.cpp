@@ -309,32 +309,49 @@ bte::StepArgs<T> step_args(const bte_handle* h) {
     return a;
 }
 
+/* Host tables of one instance (Sec. 2): row factors sigma_n I_n/(pi I_0),
+ * column factors sqrt(mu/(2 pi alpha)) exp(-mu phi^2/2) and B phi_m laid out
+ * with G ghost columns, and the FP64 drive E(i dt), E((i+1/2) dt) over one
+ * period plus two entries (Sec. 2, E(t) = E_dc + E_omega cos(omega t)). */
 template <typename T>
-int upload_tables(bte_handle* h) {
-    const bte_params& p = h->p;
-    const Layout& L = h->L;
+void build_tables(const bte_params& p, const TimeGrid& tg, int G, int pitch, double dphi,
+                  std::vector<T>& row, std::vector<T>& colg, std::vector<T>& colb,
+                  std::vector<double>& ew, std::vector<double>& ef, double& r1) {
     const int N1 = p.n_max + 1, M1 = p.m_points;
     std::vector<double> r(N1);
     miller_ratio(p.mu, p.n_max, r.data());
-    h->r1 = r[1];
-    std::vector<T> row(N1), colg(L.pitch, (T)0), colb(L.pitch, (T)0);
+    r1 = r[1];
+    row.assign(N1, (T)0);
+    colg.assign(pitch, (T)0);
+    colb.assign(pitch, (T)0);
     for (int n = 0; n < N1; ++n) row[n] = (T)((n == 0 ? 0.5 : 1.0) * r[n] / kPi);
     const double pref = std::sqrt(p.mu / (2.0 * kPi * p.alpha));
     for (int m = 0; m < M1; ++m) {
-        const double phi = p.phiy_min + m * h->dphi;
-        colg[L.G + m] = (T)(pref * std::exp(-0.5 * p.mu * phi * phi));
-        colb[L.G + m] = (T)(p.B * phi);
+        const double phi = p.phiy_min + m * dphi;
+        colg[G + m] = (T)(pref * std::exp(-0.5 * p.mu * phi * phi));
+        colb[G + m] = (T)(p.B * phi);
     }
-    const long long Pt = h->tg.P > 0 ? h->tg.P : 1;
-    std::vector<double> ew(Pt + 2), ef(Pt + 2);
+    const long long Pt = tg.P > 0 ? tg.P : 1;
+    ew.assign(Pt + 2, 0.0);
+    ef.assign(Pt + 2, 0.0);
     for (long long q = 0; q <= Pt + 1; ++q) {
-        if (h->tg.P > 0) {
+        if (tg.P > 0) {
             ew[q] = p.E_dc + p.E_omega * std::cos(kTwoPi * (double)q / (double)Pt);
             ef[q] = p.E_dc + p.E_omega * std::cos(kTwoPi * ((double)q + 0.5) / (double)Pt);
         } else {
             ew[q] = ef[q] = p.E_dc + p.E_omega;
         }
     }
+}
+
+template <typename T>
+int upload_tables(bte_handle* h) {
+    const Layout& L = h->L;
+    const int N1 = h->p.n_max + 1;
+    std::vector<T> row, colg, colb;
+    std::vector<double> ew, ef;
+    build_tables<T>(h->p, h->tg, L.G, L.pitch, h->dphi, row, colg, colb, ew, ef, h->r1);
+    const long long Pt = h->tg.P > 0 ? h->tg.P : 1;
     CU(cudaMemcpyAsync(h->ptr<T>(L.off_row_a0), row.data(), N1 * sizeof(T), cudaMemcpyHostToDevice,
                        h->stream));
     CU(cudaMemcpyAsync(h->ptr<T>(L.off_col_g), colg.data(), L.pitch * sizeof(T),
@@ -499,9 +516,392 @@ int set_grid(bte_handle* h, int grid, const double* a, const double* b) {
 
 }  // namespace
 
+/* ---------------------------------------------------------------------- */
+/* batched sweep                                                           */
+/* ---------------------------------------------------------------------- */
+namespace {
+
+struct BatchPoint {
+    int idx; /* position in the caller's array */
+    TimeGrid tg;
+    int N1, M1, ntx, nty, pitch, items;
+    double dphi;
+    size_t state_off, state_bytes, tab_off; /* within the batch workspace */
+    size_t o_row, o_colg, o_colb, o_ew, o_ef, o_part, o_ticket, o_acc; /* within the tables */
+    size_t tab_bytes;
+    double r1;
+};
+
+constexpr int kAcc = 8; /* per-instance accumulators, see BatchInst::acc */
+
+/* Runs points [first, last) of `pts` as one batch advancing in lock-step. */
+template <typename T>
+int run_batch(const bte_params* p, std::vector<BatchPoint>& pts, size_t first, size_t last,
+              int tile, int chunk, int vec, int graph_len, cudaStream_t st, cudaStream_t cap,
+              bte_obs* out) {
+    const int elem = (int)sizeof(T);
+    const int G = 128 / elem, Hp = 32 / elem;
+    /* layout: [all states][all tables, accumulators][records][counter, error] */
+    size_t o = 0;
+    int items = 0;
+    long long Kmax = 0;
+    for (size_t i = first; i < last; ++i) {
+        BatchPoint& b = pts[i];
+        b.pitch = (int)align_up((size_t)(G + b.ntx * tile + Hp), 32);
+        b.state_bytes = align_up((size_t)b.N1 * b.pitch * elem, 256);
+        b.state_off = o;
+        o += 8 * b.state_bytes;
+        b.items = b.ntx * b.nty;
+        items += b.items;
+        Kmax = std::max(Kmax, b.tg.K);
+    }
+    const size_t states_end = o;
+    for (size_t i = first; i < last; ++i) {
+        BatchPoint& b = pts[i];
+        const long long Pt = b.tg.P > 0 ? b.tg.P : 1;
+        size_t t = 0;
+        b.o_row = t;
+        t += align_up((size_t)b.N1 * elem, 256);
+        b.o_colg = t;
+        t += align_up((size_t)b.pitch * elem, 256);
+        b.o_colb = t;
+        t += align_up((size_t)b.pitch * elem, 256);
+        b.o_ew = t;
+        t += align_up((size_t)(Pt + 2) * 8, 256);
+        b.o_ef = t;
+        t += align_up((size_t)(Pt + 2) * 8, 256);
+        b.o_part = t;
+        t += align_up((size_t)2 * b.ntx * 8, 256);
+        b.o_ticket = t;
+        t += 256;
+        b.o_acc = t;
+        t += 256;
+        b.tab_bytes = t;
+        b.tab_off = o;
+        o += t;
+    }
+    const size_t tables_begin = states_end, tables_end = o;
+    const size_t n = last - first;
+    const size_t rec_off = align_up(o, 256);
+    o = rec_off + align_up(n * sizeof(bte::BatchInst<T>), 256);
+    const size_t base_off = o;
+    o += 256;
+    const size_t err_off = o;
+    o += 256;
+    const size_t total = o;
+
+    unsigned char* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BTE_ENOMEM, "batch workspace of %zu bytes: %s", total, cudaGetErrorString(e));
+    }
+    std::vector<unsigned char> host(tables_end - tables_begin, 0);
+    std::vector<bte::BatchInst<T>> rec(n);
+    int rc = BTE_OK;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    auto cleanup = [&]() {
+        for (auto& g : graph)
+            if (g) cudaGraphExecDestroy(g);
+        cudaStreamSynchronize(st);
+        cudaFree(mem);
+    };
+    int item0 = 0;
+    for (size_t i = first; i < last; ++i) {
+        BatchPoint& b = pts[i];
+        const bte_params& pp = p[b.idx];
+        std::vector<T> row, colg, colb;
+        std::vector<double> ew, ef;
+        build_tables<T>(pp, b.tg, G, b.pitch, b.dphi, row, colg, colb, ew, ef, b.r1);
+        unsigned char* hb = host.data() + (b.tab_off - tables_begin);
+        std::memcpy(hb + b.o_row, row.data(), row.size() * elem);
+        std::memcpy(hb + b.o_colg, colg.data(), colg.size() * elem);
+        std::memcpy(hb + b.o_colb, colb.data(), colb.size() * elem);
+        std::memcpy(hb + b.o_ew, ew.data(), ew.size() * 8);
+        std::memcpy(hb + b.o_ef, ef.data(), ef.size() * 8);
+        unsigned char* tb = mem + b.tab_off;
+        bte::BatchInst<T>& R = rec[i - first];
+        for (int s = 0; s < 2; ++s) {
+            R.a_w[s] = reinterpret_cast<T*>(mem + b.state_off + (4 * s + 0) * b.state_bytes);
+            R.b_w[s] = reinterpret_cast<T*>(mem + b.state_off + (4 * s + 1) * b.state_bytes);
+            R.a_f[s] = reinterpret_cast<T*>(mem + b.state_off + (4 * s + 2) * b.state_bytes);
+            R.b_f[s] = reinterpret_cast<T*>(mem + b.state_off + (4 * s + 3) * b.state_bytes);
+        }
+        R.row_a0 = reinterpret_cast<const T*>(tb + b.o_row);
+        R.col_g = reinterpret_cast<const T*>(tb + b.o_colg);
+        R.col_bphi = reinterpret_cast<const T*>(tb + b.o_colb);
+        R.e_whole = reinterpret_cast<const double*>(tb + b.o_ew);
+        R.e_frac = reinterpret_cast<const double*>(tb + b.o_ef);
+        R.part = reinterpret_cast<double*>(tb + b.o_part);
+        R.ticket = reinterpret_cast<unsigned*>(tb + b.o_ticket);
+        R.acc = reinterpret_cast<double*>(tb + b.o_acc);
+        R.K = b.tg.K;
+        R.Kw = b.tg.Kw;
+        R.N = b.N1 - 1;
+        R.M = b.M1 - 1;
+        R.pitch = b.pitch;
+        R.P = b.tg.P > 0 ? (int)b.tg.P : 1;
+        R.ntx = b.ntx;
+        R.nty = b.nty;
+        R.item0 = item0;
+        item0 += b.items;
+        const double dt = b.tg.dt_eff;
+        R.h = (T)dt;
+        R.hh = (T)(0.5 * dt);
+        R.nu = (T)(1.0 + 0.5 * dt);
+        R.xi = (T)(1.0 - 0.5 * dt);
+        R.c = (T)(pp.B * dt / (4.0 * b.dphi));
+        const double sq = std::sqrt(pp.alpha);
+        R.vscale = kPi * sq * b.dphi;
+        R.nscale = 2.0 * kPi * sq * b.dphi;
+        R.omega = pp.omega;
+        R.dt_eff = dt;
+        /* window angle: P > 0 uses 2 pi (k mod P)/P; omega == 0 has no window angle */
+        if (b.tg.P == 0) R.P = 0;
+    }
+#define BCU(call)                                                                          \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            rc = fail(BTE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));          \
+            cleanup();                                                                     \
+            return rc;                                                                     \
+        }                                                                                  \
+    } while (0)
+    BCU(cudaMemsetAsync(mem, 0, states_end, st));
+    BCU(cudaMemcpyAsync(mem + tables_begin, host.data(), host.size(), cudaMemcpyHostToDevice, st));
+    BCU(cudaMemcpyAsync(mem + rec_off, rec.data(), n * sizeof(bte::BatchInst<T>),
+                        cudaMemcpyHostToDevice, st));
+    BCU(cudaMemsetAsync(mem + base_off, 0, 512, st));
+    /* initial state and start-up half step of every instance (Sec. 2, Sec. 3) */
+    for (size_t i = first; i < last; ++i) {
+        const BatchPoint& b = pts[i];
+        const bte_params& pp = p[b.idx];
+        const bte::BatchInst<T>& R = rec[i - first];
+        int r = bte::launch_init<T>(R.a_w[0], R.b_w[0], R.row_a0, R.col_g, R.N, R.M, R.pitch, st);
+        bte::ApplyArgs<T> a;
+        a.a = R.a_w[0];
+        a.b = R.b_w[0];
+        a.as = R.a_w[0];
+        a.bs = R.b_w[0];
+        a.an = R.a_f[0];
+        a.bn = R.b_f[0];
+        a.row_a0 = R.row_a0;
+        a.col_g = R.col_g;
+        a.col_bphi = R.col_bphi;
+        a.N = R.N;
+        a.M = R.M;
+        a.pitch = R.pitch;
+        const double hs = 0.5 * b.tg.dt_eff;
+        a.E_start = pp.E_dc + pp.E_omega;
+        a.E_end = pp.E_dc + pp.E_omega * std::cos(pp.omega * hs);
+        a.h = (T)hs;
+        a.hh = (T)(0.5 * hs);
+        a.nu = (T)(1.0 + 0.5 * hs);
+        a.xi = (T)(1.0 - 0.5 * hs);
+        a.c = (T)(pp.B * hs / (4.0 * b.dphi));
+        if (!r) r = bte::launch_apply<T>(a, st);
+        if (!r)
+            r = bte::launch_observe<T>(R.a_w[0], R.b_w[0], R.M, R.pitch, R.vscale, R.nscale,
+                                       R.acc + 6, R.acc + 7, 0, st);
+        if (r) {
+            rc = fail(BTE_ECUDA, "batch initialisation: %s", cudaGetErrorString((cudaError_t)r));
+            cleanup();
+            return rc;
+        }
+    }
+    /* lock-step advance: graphs of graph_len launches, then single launches */
+    bte::BatchArgs<T> ba;
+    ba.inst = reinterpret_cast<const bte::BatchInst<T>*>(mem + rec_off);
+    ba.ninst = (int)n;
+    ba.items = items;
+    ba.base = reinterpret_cast<const long long*>(mem + base_off);
+    ba.err = reinterpret_cast<int*>(mem + err_off);
+    ba.tile_m = tile;
+    ba.chunk_n = chunk;
+    ba.vec = vec;
+    {
+        int bps = 0, dev = 0, sms = 0;
+        BCU(cudaGetDevice(&dev));
+        BCU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        int r = bte::step_kernel_configure_batch<T>(tile, chunk, vec, &bps);
+        if (r || bps < 1) {
+            rc = fail(BTE_ECUDA, "batch kernel configure failed");
+            cleanup();
+            return rc;
+        }
+        ba.grid = std::min(items, bps * sms);
+    }
+    long long* base = reinterpret_cast<long long*>(mem + base_off);
+    int set = 0;
+    long long left = Kmax;
+    const int L = (int)std::min<long long>(graph_len, Kmax);
+    while (L >= 2 && left >= L) {
+        if (!graph[set]) {
+            cudaGraph_t g = nullptr;
+            BCU(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+            int r = 0;
+            for (int i = 0; i < L && !r; ++i) r = bte::launch_step_batch<T>(ba, i, set, i > 0, cap);
+            if (!r) r = bte::launch_advance_base(base, L, cap);
+            cudaError_t ee = cudaStreamEndCapture(cap, &g);
+            if (r || ee != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                rc = fail(BTE_ECUDA, "batch graph capture failed");
+                cleanup();
+                return rc;
+            }
+            ee = cudaGraphInstantiate(&graph[set], g, 0);
+            cudaGraphDestroy(g);
+            if (ee != cudaSuccess) {
+                graph[set] = nullptr;
+                rc = fail(BTE_ECUDA, "batch graph instantiate failed");
+                cleanup();
+                return rc;
+            }
+        }
+        BCU(cudaGraphLaunch(graph[set], st));
+        left -= L;
+        set ^= L & 1;
+    }
+    if (left > 0) {
+        int r = 0;
+        for (long long i = 0; i < left && !r; ++i)
+            r = bte::launch_step_batch<T>(ba, (int)i, set, i > 0, st);
+        if (!r) r = bte::launch_advance_base(base, left, st);
+        if (r) {
+            rc = fail(BTE_ECUDA, "batch step: %s", cudaGetErrorString((cudaError_t)r));
+            cleanup();
+            return rc;
+        }
+    }
+    /* window averages and status of every instance */
+    std::vector<unsigned char> acc_host(tables_end - tables_begin);
+    int err = 0;
+    BCU(cudaMemcpyAsync(acc_host.data(), mem + tables_begin, acc_host.size(),
+                        cudaMemcpyDeviceToHost, st));
+    BCU(cudaMemcpyAsync(&err, mem + err_off, sizeof err, cudaMemcpyDeviceToHost, st));
+    BCU(cudaStreamSynchronize(st));
+#undef BCU
+    int worst = BTE_OK;
+    for (size_t i = first; i < last; ++i) {
+        const BatchPoint& b = pts[i];
+        const bte_params& pp = p[b.idx];
+        double acc[kAcc];
+        std::memcpy(acc, acc_host.data() + (b.tab_off - tables_begin) + b.o_acc, sizeof acc);
+        bte_obs& ob = out[b.idx];
+        std::memset(&ob, 0, sizeof ob);
+        ob.t = b.tg.K * b.tg.dt_eff;
+        ob.step = b.tg.K;
+        ob.v_dr = acc[4];
+        ob.norm = acc[5];
+        ob.v_dc_avg = acc[1] / (double)b.tg.Kw;
+        ob.absorption = pp.omega > 0 ? 2.0 / b.r1 * acc[0] / (double)b.tg.Kw : NAN;
+        ob.norm_max_abs_err = std::fmax(acc[2], std::fabs(acc[7] - 1.0));
+        ob.dt_eff = b.tg.dt_eff;
+        ob.steps_total = b.tg.K;
+        ob.steps_per_period = b.tg.P;
+        ob.window_steps = b.tg.Kw;
+        int s = BTE_OK;
+        if (err) s = BTE_ETIMEOUT;
+        else if (acc[3] != 0.0 || !std::isfinite(acc[6]) || !std::isfinite(acc[7]) ||
+                 !(ob.norm_max_abs_err <= 0.05))
+            s = BTE_EUNSTABLE;
+        ob.status = s;
+        if (s != BTE_OK && (worst == BTE_OK || s == BTE_ETIMEOUT)) worst = s;
+    }
+    cleanup();
+    return worst;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* bte_last_error(void) { return g_err.c_str(); }
+
+int bte_batch_run(const bte_params* p, int32_t n, bte_obs* out, const bte_batch_opts* opts) {
+    if (!p || !out || n < 0) return fail(BTE_EINVAL, "bte_batch_run: bad argument");
+    if (n == 0) return BTE_OK;
+    const int prec = p[0].precision;
+    std::vector<BatchPoint> pts(n);
+    for (int i = 0; i < n; ++i) {
+        int rc = validate(&p[i]);
+        if (rc) return fail(rc, "point %d: %s", i, g_err.c_str());
+        if (p[i].precision != prec) return fail(BTE_EINVAL, "all points must share one precision");
+        BatchPoint& b = pts[i];
+        b.idx = i;
+        rc = time_grid(&p[i], b.tg);
+        if (rc) return fail(rc, "point %d: %s", i, g_err.c_str());
+        b.N1 = p[i].n_max + 1;
+        b.M1 = p[i].m_points;
+        b.dphi = (p[i].phiy_max - p[i].phiy_min) / (p[i].m_points - 1);
+    }
+    const bool fp64 = prec == BTE_FP64;
+    int vec = (opts && opts->vec) ? opts->vec : (fp64 ? 2 : 4);
+    if (vec != 2 && vec != 4) return fail(BTE_EINVAL, "vec must be 2 or 4");
+    if (fp64 && vec != 2) return fail(BTE_EINVAL, "FP64 runs with vec = 2");
+    const int tile = (opts && opts->tile_m) ? opts->tile_m : 32 * vec;
+    const int chunk = (opts && opts->chunk_n) ? opts->chunk_n : 16;
+    const int max_tile = fp64 ? bte::step_max_tile<double>(vec) : bte::step_max_tile<float>(vec);
+    if (tile % 4 || tile < 32 || tile > max_tile)
+        return fail(BTE_EINVAL, "tile_m must be a multiple of 4 in 32..%d", max_tile);
+    if (chunk < 4) return fail(BTE_EINVAL, "chunk_n must be >= 4");
+    const size_t smem = fp64 ? bte::step_smem_bytes<double>(tile, chunk, vec)
+                             : bte::step_smem_bytes<float>(tile, chunk, vec);
+    if (smem > 227 * 1024)
+        return fail(BTE_EINVAL, "tile_m %d needs %zu bytes of shared memory", tile, smem);
+    const int graph_len = (opts && opts->graph_steps > 0) ? opts->graph_steps : 1024;
+    const int max_batch = (opts && opts->max_batch > 0) ? opts->max_batch : 1024;
+    const long long max_bytes =
+        (opts && opts->max_batch_bytes > 0) ? opts->max_batch_bytes : (4ll << 30);
+    for (auto& b : pts) {
+        b.ntx = (b.M1 + tile - 1) / tile;
+        b.nty = (b.N1 + chunk - 1) / chunk;
+    }
+    /* longest runs first, so a batch's members need similar step counts */
+    std::sort(pts.begin(), pts.end(), [](const BatchPoint& x, const BatchPoint& y) {
+        return x.tg.K != y.tg.K ? x.tg.K > y.tg.K : x.idx < y.idx;
+    });
+    cudaStream_t st = opts && opts->stream ? (cudaStream_t)opts->stream : nullptr;
+    bool own = false;
+    if (!st) {
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(BTE_ECUDA, "cudaStreamCreate failed");
+        own = true;
+    }
+    cudaStream_t cap = nullptr;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+        if (own) cudaStreamDestroy(st);
+        return fail(BTE_ECUDA, "cudaStreamCreate failed");
+    }
+    const int elem = fp64 ? 8 : 4;
+    int worst = BTE_OK;
+    size_t first = 0;
+    while (first < pts.size()) {
+        size_t last = first;
+        long long bytes = 0;
+        while (last < pts.size() && (int)(last - first) < max_batch) {
+            const BatchPoint& b = pts[last];
+            const long long pitch = (long long)align_up((size_t)(128 / elem + b.ntx * tile + 32 / elem), 32);
+            const long long sb = 8ll * b.N1 * pitch * elem + 2ll * (b.tg.P + 2) * 8 + 4096;
+            if (last > first && bytes + sb > max_bytes) break;
+            bytes += sb;
+            ++last;
+        }
+        const int rc = fp64 ? run_batch<double>(p, pts, first, last, tile, chunk, vec, graph_len, st, cap, out)
+                            : run_batch<float>(p, pts, first, last, tile, chunk, vec, graph_len, st, cap, out);
+        if (rc == BTE_ECUDA || rc == BTE_ENOMEM) {
+            worst = rc;
+            break;
+        }
+        if (rc != BTE_OK && (worst == BTE_OK || rc == BTE_ETIMEOUT)) worst = rc;
+        first = last;
+    }
+    cudaStreamDestroy(cap);
+    if (own) cudaStreamDestroy(st);
+    if (worst != BTE_OK && g_err.empty()) fail(worst, "at least one point failed");
+    return worst;
+}
 
 const char* bte_version(void) { return "bte-gb300 0.1 (sm_103a)"; }
 

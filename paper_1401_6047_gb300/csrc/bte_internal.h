@@ -56,6 +56,44 @@ struct StepArgs {
     double vscale, nscale;/* pi sqrt(alpha) dphi, 2 pi sqrt(alpha) dphi          */
 };
 
+/* One instance of a batched launch (device array, one record per instance).
+ * All instances of a batch share tile_m / chunk_n / vec and advance in
+ * lock-step (step base + i); an instance whose K steps are done is skipped.
+ * Instead of a trace, the instance accumulates the window sums in FP64. */
+template <typename T>
+struct BatchInst {
+    T* a_w[2];
+    T* b_w[2];
+    T* a_f[2];
+    T* b_f[2];
+    const T* row_a0;
+    const T* col_g;
+    const T* col_bphi;
+    const double* e_whole;
+    const double* e_frac;
+    double* part;         /* [2][ntx] per-tile partial sums                      */
+    unsigned* ticket;     /* arrival counter of the row-0 items                  */
+    double* acc;          /* [8]: sum v cos(omega t) and sum v over the window,
+                             max |norm-1|, non-finite flag, v and norm of the
+                             latest step, v and norm of step 0               */
+    long long K, Kw;      /* steps of the run, window samples                    */
+    int N, M, pitch, P, ntx, nty;
+    int item0;            /* index of the instance's first work item            */
+    T h, hh, nu, xi, c;
+    double vscale, nscale;
+    double omega, dt_eff;
+};
+
+/* Arguments of a batched launch. */
+template <typename T>
+struct BatchArgs {
+    const BatchInst<T>* inst;
+    int ninst, items;     /* instances; total work items                         */
+    const long long* base;/* common step counter                                 */
+    int* err;
+    int tile_m, chunk_n, vec, grid;
+};
+
 /* One plain application of T (start-up half step), unfused. */
 template <typename T>
 struct ApplyArgs {
@@ -89,6 +127,11 @@ int launch_apply(const ApplyArgs<T>& a, void* stream);
  * overlaps the previous launch). */
 template <typename T>
 int launch_step(const StepArgs<T>& a, int i, int parity, bool pdl, void* stream);
+/* Batched form: every active instance of the batch advances one step. */
+template <typename T>
+int launch_step_batch(const BatchArgs<T>& a, int i, int parity, bool pdl, void* stream);
+template <typename T>
+int step_kernel_configure_batch(int tile_m, int chunk_n, int vec, int* blocks_per_sm);
 template <typename T>
 int launch_observe(const T* a_w, const T* b_w, int M, int pitch, double vscale,
                    double nscale, double* trace_v, double* trace_n, long long slot,

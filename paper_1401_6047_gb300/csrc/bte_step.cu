@@ -10,11 +10,14 @@
  *     B^t_{n,m} = c (D b_{n+1} - D b_{n-1}),  A^t_{n,m} = c (chi(n) D a_{n-1} - D a_{n+1}),
  *     c = B dt / (4 dphi).
  *
- * Work items.  The grid is cut into items of tile_m phi_y columns x chunk_n
+ * Work items.  A grid is cut into items of tile_m phi_y columns x chunk_n
  * harmonic rows.  Persistent CTAs take items q = blockIdx.x, +gridDim.x, ...
  * An item is walked upward in n with a one-row lag: at row j the CTA builds
  * the new whole-grid row j (its columns plus one halo column per side) and
  * then the new fractional row j-1, which needs the new whole rows j-2 and j.
+ * In the batched form the items of many instances (parameter points, each
+ * with its own grid, time step and drive) share one launch; an item first
+ * looks up its instance.
  *
  * Threads.  Compute thread t owns V consecutive columns (V = 2 or 4) of the
  * tile.  One extra warp (the producer) issues the TMA bulk copies that
@@ -29,14 +32,15 @@
  * registers to global memory; the new fractional row goes from registers to
  * global memory.  One __syncthreads per row.
  *
- * Launch.  Programmatic dependent launch: the prologue (barrier set-up,
- * drive values) runs while the previous step drains; griddepcontrol.wait
- * precedes the first read of the state.
+ * Launch.  Programmatic dependent launch: the prologue (barrier set-up)
+ * runs while the previous step drains; griddepcontrol.wait precedes the
+ * first read of the state.
  *
  * Observables (Sec. 2, Eqs. v_dr_generic and norm_in_phi): items that own
  * rows 0 and 1 reduce sum_m a_{0,m} and sum_m b_{1,m} in FP64; the last of
- * them to arrive adds the per-tile partials in tile order, so the trace is
- * bitwise reproducible.
+ * them to arrive adds the per-tile partials in tile order, so the results
+ * are bitwise reproducible.  A single instance writes the sample to its
+ * trace; a batched instance adds it to its window sums (Eq. absorption_def).
  *
  * Every mbarrier wait is bounded (~2 s of %globaltimer); on expiry the kernel
  * records an error word that the host reports as BTE_ETIMEOUT.
@@ -152,21 +156,121 @@ __device__ __forceinline__ void pdl_trigger() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-template <typename T, int V>
+/* What an item needs to know about its instance for the current step. */
+template <typename T>
+struct View {
+    const T *gFa, *gFb, *gWa, *gWb; /* old state (set cur)          */
+    T *oWa, *oFa;                    /* new state (set nxt)          */
+    size_t dWb, dFb;                 /* b array offset from a array  */
+    const T *row_a0, *col_g, *col_bphi;
+    double *part;
+    unsigned* ticket;
+    int N, M, pitch, ntx, inst, q0; /* q0: the instance's first item */
+    long long k;
+    bool active;                     /* instance still running       */
+    T Ews, Ewe, Efs, Efe, h, hh, nu, xi, cc;
+};
+
+/* Instance of item q: single-instance launches use A; batched ones search
+ * the records by first item index. */
+template <typename T, bool BATCH>
+__device__ __forceinline__ void make_view(View<T>& v, int q, const StepArgs<T>& A,
+                                          const BatchArgs<T>& Bt, long long kbase, int cur,
+                                          bool with_drive) {
+    if constexpr (!BATCH) {
+        v.gFa = A.a_f[cur];
+        v.gFb = A.b_f[cur];
+        v.gWa = A.a_w[cur];
+        v.gWb = A.b_w[cur];
+        v.oWa = A.a_w[cur ^ 1];
+        v.oFa = A.a_f[cur ^ 1];
+        v.dWb = (size_t)(A.b_w[cur ^ 1] - v.oWa);
+        v.dFb = (size_t)(A.b_f[cur ^ 1] - v.oFa);
+        v.row_a0 = A.row_a0;
+        v.col_g = A.col_g;
+        v.col_bphi = A.col_bphi;
+        v.part = A.part;
+        v.ticket = A.ticket;
+        v.N = A.N;
+        v.M = A.M;
+        v.pitch = A.pitch;
+        v.ntx = A.ntx;
+        v.inst = 0;
+        v.q0 = 0;
+        v.k = kbase;
+        v.active = true;
+        if (with_drive) {
+            const int kk = A.P > 0 ? (int)(kbase % A.P) : 0;
+            v.Ews = (T)A.e_whole[kk];
+            v.Ewe = (T)A.e_whole[kk + 1];
+            v.Efs = (T)A.e_frac[kk];
+            v.Efe = (T)A.e_frac[kk + 1];
+            v.h = A.h;
+            v.hh = A.hh;
+            v.nu = A.nu;
+            v.xi = A.xi;
+            v.cc = A.c;
+        }
+    } else {
+        int lo = 0, hi = Bt.ninst - 1; /* last instance with item0 <= q */
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (Bt.inst[mid].item0 <= q) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchInst<T>& I = Bt.inst[lo];
+        v.inst = lo;
+        v.q0 = I.item0;
+        v.gFa = I.a_f[cur];
+        v.gFb = I.b_f[cur];
+        v.gWa = I.a_w[cur];
+        v.gWb = I.b_w[cur];
+        v.oWa = I.a_w[cur ^ 1];
+        v.oFa = I.a_f[cur ^ 1];
+        v.dWb = (size_t)(I.b_w[cur ^ 1] - v.oWa);
+        v.dFb = (size_t)(I.b_f[cur ^ 1] - v.oFa);
+        v.row_a0 = I.row_a0;
+        v.col_g = I.col_g;
+        v.col_bphi = I.col_bphi;
+        v.part = I.part;
+        v.ticket = I.ticket;
+        v.N = I.N;
+        v.M = I.M;
+        v.pitch = I.pitch;
+        v.ntx = I.ntx;
+        v.k = kbase;
+        v.active = kbase < I.K;
+        if (with_drive && v.active) {
+            const int kk = I.P > 0 ? (int)(kbase % I.P) : 0;
+            v.Ews = (T)I.e_whole[kk];
+            v.Ewe = (T)I.e_whole[kk + 1];
+            v.Efs = (T)I.e_frac[kk];
+            v.Efe = (T)I.e_frac[kk + 1];
+            v.h = I.h;
+            v.hh = I.hh;
+            v.nu = I.nu;
+            v.xi = I.xi;
+            v.cc = I.c;
+        }
+    }
+}
+
+template <typename T, int V, bool BATCH>
 __global__ void __launch_bounds__(MaxBlock<T, V>::value)
-    fused_step_kernel(StepArgs<T> A, int launch_i, int parity) {
+    fused_step_kernel(StepArgs<T> A, BatchArgs<T> Bt, int launch_i, int parity) {
     constexpr int H = StepCfg<T>::H;
     constexpr int G = StepCfg<T>::G;
     constexpr int RS = StepCfg<T>::RS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
 
-    const int Wt = A.tile_m;
+    const int Wt = BATCH ? Bt.tile_m : A.tile_m;
+    const int chunk = BATCH ? Bt.chunk_n : A.chunk_n;
     const int NT = Wt / V;
     const int NTr = round_warp(NT);
     const int LW = Wt + 2 * H;
     const int WN = Wt + 2 * V;
     size_t offN, offR, offBar, offRed;
-    smem_layout<T>(Wt, A.chunk_n, V, &offN, &offR, &offBar, &offRed);
+    smem_layout<T>(Wt, chunk, V, &offN, &offR, &offBar, &offRed);
     T* sF = reinterpret_cast<T*>(smem_raw);        /* [RS][2][LW] */
     T* sW = sF + (size_t)RS * 2 * LW;              /* [RS][2][LW] */
     T* sN = reinterpret_cast<T*>(smem_raw + offN); /* [2][2][WN]  */
@@ -178,10 +282,8 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
     const bool is_comp = tid < NT;
     const bool is_prod = tid >= NTr;
     const int lane = tid & 31;
-    const int N = A.N, M = A.M, pitch = A.pitch;
-    const int ntx = A.ntx;
-    const int items = A.ntx * A.nty;
-    const int cur = (parity + launch_i) & 1, nxt = cur ^ 1;
+    const int items = BATCH ? Bt.items : A.ntx * A.nty;
+    const int cur = (parity + launch_i) & 1;
     const uint32_t rowbytes = (uint32_t)(LW * sizeof(T));
 
     pdl_trigger();
@@ -191,53 +293,59 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
     }
     /* new-row buffers: entries outside the tile's columns +-1 stay zero */
     for (int q = tid; q < 4 * WN; q += blockDim.x) sN[q] = (T)0;
-
-    const long long k = *A.base + launch_i; /* only the counter kernel moves base */
-    const int kk = A.P > 0 ? (int)(k % A.P) : 0;
-    const T Ews = (T)A.e_whole[kk], Ewe = (T)A.e_whole[kk + 1];
-    const T Efs = (T)A.e_frac[kk], Efe = (T)A.e_frac[kk + 1];
-    const T h = A.h, hh = A.hh, nu = A.nu, xi = A.xi, cc = A.c;
-    const T* gFa = A.a_f[cur];
-    const T* gFb = A.b_f[cur];
-    const T* gWa = A.a_w[cur];
-    const T* gWb = A.b_w[cur];
-    T* oWa = A.a_w[nxt];
-    T* oFa = A.a_f[nxt];
-    const size_t dWb = (size_t)(A.b_w[nxt] - oWa), dFb = (size_t)(A.b_f[nxt] - oFa);
+    /* only the counter kernel moves base */
+    const long long kbase = *(BATCH ? Bt.base : A.base) + launch_i;
     __syncthreads();
 
     /* everything below reads the previous step's state */
     pdl_wait();
 
     /* ---- producer: issues the global stage sequence of this CTA's items ---- */
-    int p_item = blockIdx.x, p_s = 0, p_S = 0, p_n0 = 0, p_n1 = 0;
-    size_t p_col0 = 0;
+    int p_item = blockIdx.x, p_s = 0, p_S = 0, p_n0 = 0, p_n1 = 0, p_N = 0;
+    size_t p_col0 = 0, p_pitch = 0;
+    const T *p_Fa = nullptr, *p_Fb = nullptr, *p_Wa = nullptr, *p_Wb = nullptr;
     int p_slot = 0;
     long long p_issued = 0, p_freed = 0;
+    /* first item at or after p_item whose instance is still running */
     auto p_load_item = [&]() {
-        const int ty = p_item / ntx;
-        p_n0 = ty * A.chunk_n;
-        p_n1 = min(p_n0 + A.chunk_n, N + 1);
-        p_S = p_n1 - p_n0 + 4;
-        p_col0 = (size_t)(p_item - ty * ntx) * Wt + (G - H);
+        while (p_item < items) {
+            View<T> v;
+            make_view<T, BATCH>(v, p_item, A, Bt, kbase, cur, false);
+            if (v.active) {
+                const int ql = p_item - v.q0;
+                const int ty = ql / v.ntx;
+                p_n0 = ty * chunk;
+                p_n1 = min(p_n0 + chunk, v.N + 1);
+                p_S = p_n1 - p_n0 + 4;
+                p_N = v.N;
+                p_pitch = (size_t)v.pitch;
+                p_col0 = (size_t)(ql - ty * v.ntx) * Wt + (G - H);
+                p_Fa = v.gFa;
+                p_Fb = v.gFb;
+                p_Wa = v.gWa;
+                p_Wb = v.gWb;
+                return;
+            }
+            p_item += gridDim.x;
+        }
     };
     auto pump = [&]() {
         while (p_item < items && p_issued < p_freed + RS) {
             const int row = p_n0 - 2 + p_s;
             const uint32_t mb = smem_u32(&bar[p_slot]);
-            if (row < 0 || row > N) {
+            if (row < 0 || row > p_N) {
                 mbar_arrive(mb);
             } else {
                 const bool wneed = row >= p_n0 - 1 && row <= p_n1;
                 mbar_arrive_tx(mb, rowbytes * (wneed ? 4u : 2u));
-                const size_t off = (size_t)row * pitch + p_col0;
+                const size_t off = (size_t)row * p_pitch + p_col0;
                 T* dF = sF + (size_t)p_slot * 2 * LW;
-                bulk_g2s(smem_u32(dF), gFa + off, rowbytes, mb);
-                bulk_g2s(smem_u32(dF + LW), gFb + off, rowbytes, mb);
+                bulk_g2s(smem_u32(dF), p_Fa + off, rowbytes, mb);
+                bulk_g2s(smem_u32(dF + LW), p_Fb + off, rowbytes, mb);
                 if (wneed) {
                     T* dW = sW + (size_t)p_slot * 2 * LW;
-                    bulk_g2s(smem_u32(dW), gWa + off, rowbytes, mb);
-                    bulk_g2s(smem_u32(dW + LW), gWb + off, rowbytes, mb);
+                    bulk_g2s(smem_u32(dW), p_Wa + off, rowbytes, mb);
+                    bulk_g2s(smem_u32(dW + LW), p_Wb + off, rowbytes, mb);
                 }
             }
             ++p_issued;
@@ -245,11 +353,11 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
             if (++p_s == p_S) {
                 p_s = 0;
                 p_item += gridDim.x;
-                if (p_item < items) p_load_item();
+                p_load_item();
             }
         }
     };
-    if (tid == NTr && p_item < items) {
+    if (tid == NTr) {
         p_load_item();
         pump();
     }
@@ -260,17 +368,23 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
     uint32_t c_phase = 0;
 
     for (int q = blockIdx.x; q < items; q += gridDim.x) {
-        const int ty = q / ntx;
-        const int tx = q - ty * ntx;
-        const int n0 = ty * A.chunk_n;
-        const int n1 = min(n0 + A.chunk_n, N + 1);
+        View<T> I;
+        make_view<T, BATCH>(I, q, A, Bt, kbase, cur, true);
+        if (!I.active) continue; /* uniform: every thread sees the same instance */
+        const int N = I.N, M = I.M, pitch = I.pitch, ntx = I.ntx;
+        const int ql = q - I.q0;
+        const int ty = ql / ntx;
+        const int tx = ql - ty * ntx;
+        const int n0 = ty * chunk;
+        const int n1 = min(n0 + chunk, N + 1);
         const int S = n1 - n0 + 4;
         const int p0 = G + tx * Wt; /* physical column of the tile's first column */
+        const T h = I.h, hh = I.hh, nu = I.nu, xi = I.xi, cc = I.cc;
 
         __syncthreads(); /* the previous item is done with sR and sN */
         for (int r = tid; r < n1 - n0 + 2; r += blockDim.x) {
             const int n = n0 - 1 + r;
-            sR[r] = (n >= 0 && n <= N) ? A.row_a0[n] : (T)0;
+            sR[r] = (n >= 0 && n <= N) ? I.row_a0[n] : (T)0;
         }
 
         /* per-column constants of the thread's V columns */
@@ -282,12 +396,12 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
 #pragma unroll
         for (int e = 0; e < V; ++e) {
             ok[e] = is_comp && (c + e - G) <= M;
-            const T bp = ok[e] ? A.col_bphi[c + e] : (T)0;
-            g[e] = ok[e] ? A.col_g[c + e] : (T)0;
-            ws[e] = (Ews + bp) * hh;
-            we[e] = (Ewe + bp) * hh;
-            fs[e] = (Efs + bp) * hh;
-            fe[e] = (Efe + bp) * hh;
+            const T bp = ok[e] ? I.col_bphi[c + e] : (T)0;
+            g[e] = ok[e] ? I.col_g[c + e] : (T)0;
+            ws[e] = (I.Ews + bp) * hh;
+            we[e] = (I.Ewe + bp) * hh;
+            fs[e] = (I.Efs + bp) * hh;
+            fe[e] = (I.Efe + bp) * hh;
         }
         const bool all_ok = ok[V - 1];
 
@@ -298,10 +412,10 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
         const int hidx = (lane == 0) ? V - 1 : V + Wt;
         T hg = 0, hbs = 0, hbe = 0;
         if (hok) {
-            hg = A.col_g[hcol];
-            const T bp = A.col_bphi[hcol];
-            hbs = (Ews + bp) * hh;
-            hbe = (Ewe + bp) * hh;
+            hg = I.col_g[hcol];
+            const T bp = I.col_bphi[hcol];
+            hbs = (I.Ews + bp) * hh;
+            hbe = (I.Ewe + bp) * hh;
         }
         __syncthreads(); /* sR ready */
 
@@ -366,16 +480,16 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
                         st_own<T, V>(na + ln, wa_n);
                         st_own<T, V>(na + WN + ln, wb_n);
                         if (j >= n0 && j < n1) {
-                            T* wrow = oWa + (size_t)j * pitch + c;
+                            T* wrow = I.oWa + (size_t)j * pitch + c;
                             if (all_ok) {
                                 st_own<T, V>(wrow, wa_n);
-                                st_own<T, V>(wrow + dWb, wb_n);
+                                st_own<T, V>(wrow + I.dWb, wb_n);
                             } else {
 #pragma unroll
                                 for (int e = 0; e < V; ++e)
                                     if (ok[e]) {
                                         wrow[e] = wa_n[e];
-                                        wrow[dWb + e] = wb_n[e];
+                                        wrow[I.dWb + e] = wb_n[e];
                                     }
                             }
                         }
@@ -438,16 +552,16 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
                                    nf * fe[e], nu, xi, h, fa_n[e], fb_n[e]);
                         if (r == 0) fb_n[e] = (T)0;
                     }
-                    T* frow = oFa + (size_t)r * pitch + c;
+                    T* frow = I.oFa + (size_t)r * pitch + c;
                     if (all_ok) {
                         st_own<T, V>(frow, fa_n);
-                        st_own<T, V>(frow + dFb, fb_n);
+                        st_own<T, V>(frow + I.dFb, fb_n);
                     } else {
 #pragma unroll
                         for (int e = 0; e < V; ++e)
                             if (ok[e]) {
                                 frow[e] = fa_n[e];
-                                frow[dFb + e] = fb_n[e];
+                                frow[I.dFb + e] = fb_n[e];
                             }
                     }
                 }
@@ -457,21 +571,42 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
                     const double sn = block_sum(part_n, red);
                     const double sv = block_sum(part_v, red);
                     if (tid == 0) {
-                        A.part[tx] = sn;
-                        A.part[ntx + tx] = sv;
+                        I.part[tx] = sn;
+                        I.part[ntx + tx] = sv;
                         __threadfence();
-                        const unsigned t = atomicAdd(A.ticket, 1u);
+                        const unsigned t = atomicAdd(I.ticket, 1u);
                         if (t == (unsigned)(ntx - 1)) {
                             __threadfence();
                             double s_n = 0, s_v = 0;
-                            const volatile double* pv = A.part;
+                            const volatile double* pv = I.part;
                             for (int u = 0; u < ntx; ++u) {
                                 s_n += pv[u];
                                 s_v += pv[ntx + u];
                             }
-                            A.trace_n[k + 1] = A.nscale * s_n;
-                            A.trace_v[k + 1] = A.vscale * s_v;
-                            *A.ticket = 0u;
+                            if constexpr (!BATCH) {
+                                A.trace_n[kbase + 1] = A.nscale * s_n;
+                                A.trace_v[kbase + 1] = A.vscale * s_v;
+                            } else {
+                                /* window sums of Eq. absorption_def, FP64, one writer
+                                 * per instance and step */
+                                const BatchInst<T>& B = Bt.inst[I.inst];
+                                const double vv = B.vscale * s_v, nn = B.nscale * s_n;
+                                const long long k1 = kbase + 1;
+                                double* acc = B.acc;
+                                if (k1 > B.K - B.Kw) {
+                                    const double ang =
+                                        B.P > 0 ? 6.283185307179586476925286766559 *
+                                                      (double)(k1 % B.P) / (double)B.P
+                                                : B.omega * (double)k1 * B.dt_eff;
+                                    acc[0] += vv * cos(ang);
+                                    acc[1] += vv;
+                                }
+                                acc[2] = fmax(acc[2], fabs(nn - 1.0));
+                                if (!isfinite(vv) || !isfinite(nn)) acc[3] = 1.0;
+                                acc[4] = vv;
+                                acc[5] = nn;
+                            }
+                            *I.ticket = 0u;
                         }
                     }
                 }
@@ -503,7 +638,7 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
         }
         cbase += S;
     }
-    if (timed_out) atomicExch(A.err, kErrTimeout);
+    if (timed_out) atomicExch(BATCH ? Bt.err : A.err, kErrTimeout);
 }
 
 }  // namespace
@@ -528,19 +663,19 @@ int step_max_tile(int vec) {
     return 2 * (MaxBlock<double, 2>::value - 32);
 }
 
-template <typename T>
+template <typename T, bool BATCH>
 static const void* step_fn(int vec) {
     if constexpr (sizeof(T) == 4)
-        return vec == 4 ? reinterpret_cast<const void*>(&fused_step_kernel<float, 4>)
-                        : reinterpret_cast<const void*>(&fused_step_kernel<float, 2>);
+        return vec == 4 ? reinterpret_cast<const void*>(&fused_step_kernel<float, 4, BATCH>)
+                        : reinterpret_cast<const void*>(&fused_step_kernel<float, 2, BATCH>);
     else
-        return reinterpret_cast<const void*>(&fused_step_kernel<double, 2>);
+        return reinterpret_cast<const void*>(&fused_step_kernel<double, 2, BATCH>);
 }
 
-template <typename T>
-int step_kernel_configure(int tile_m, int chunk_n, int vec, int* blocks_per_sm) {
+template <typename T, bool BATCH>
+static int configure(int tile_m, int chunk_n, int vec, int* blocks_per_sm) {
     const size_t bytes = step_smem_bytes<T>(tile_m, chunk_n, vec);
-    const void* fn = step_fn<T>(vec);
+    const void* fn = step_fn<T, BATCH>(vec);
     cudaError_t e =
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;
@@ -553,11 +688,22 @@ int step_kernel_configure(int tile_m, int chunk_n, int vec, int* blocks_per_sm) 
 }
 
 template <typename T>
-int launch_step(const StepArgs<T>& a, int i, int parity, bool pdl, void* stream) {
+int step_kernel_configure(int tile_m, int chunk_n, int vec, int* blocks_per_sm) {
+    return configure<T, false>(tile_m, chunk_n, vec, blocks_per_sm);
+}
+
+template <typename T>
+int step_kernel_configure_batch(int tile_m, int chunk_n, int vec, int* blocks_per_sm) {
+    return configure<T, true>(tile_m, chunk_n, vec, blocks_per_sm);
+}
+
+template <typename T, bool BATCH>
+static int launch(const StepArgs<T>& a, const BatchArgs<T>& b, int grid, int tile_m, int chunk_n,
+                  int vec, int i, int parity, bool pdl, void* stream) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(a.grid);
-    cfg.blockDim = dim3(step_block_threads<T>(a.tile_m, a.vec));
-    cfg.dynamicSmemBytes = step_smem_bytes<T>(a.tile_m, a.chunk_n, a.vec);
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(step_block_threads<T>(tile_m, vec));
+    cfg.dynamicSmemBytes = step_smem_bytes<T>(tile_m, chunk_n, vec);
     cfg.stream = (cudaStream_t)stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -566,23 +712,37 @@ int launch_step(const StepArgs<T>& a, int i, int parity, bool pdl, void* stream)
     cfg.numAttrs = 1;
     cudaError_t e;
     if constexpr (sizeof(T) == 4) {
-        if (a.vec == 4)
-            e = cudaLaunchKernelEx(&cfg, fused_step_kernel<float, 4>, a, i, parity);
+        if (vec == 4)
+            e = cudaLaunchKernelEx(&cfg, fused_step_kernel<float, 4, BATCH>, a, b, i, parity);
         else
-            e = cudaLaunchKernelEx(&cfg, fused_step_kernel<float, 2>, a, i, parity);
+            e = cudaLaunchKernelEx(&cfg, fused_step_kernel<float, 2, BATCH>, a, b, i, parity);
     } else {
-        e = cudaLaunchKernelEx(&cfg, fused_step_kernel<double, 2>, a, i, parity);
+        e = cudaLaunchKernelEx(&cfg, fused_step_kernel<double, 2, BATCH>, a, b, i, parity);
     }
     if (e != cudaSuccess) return (int)e;
     return ok_or(cudaGetLastError());
 }
 
-#define BTE_STEP_INSTANTIATE(T)                                 \
-    template size_t step_smem_bytes<T>(int, int, int);          \
-    template int step_block_threads<T>(int, int);               \
-    template int step_max_tile<T>(int);                         \
-    template int step_kernel_configure<T>(int, int, int, int*); \
-    template int launch_step<T>(const StepArgs<T>&, int, int, bool, void*);
+template <typename T>
+int launch_step(const StepArgs<T>& a, int i, int parity, bool pdl, void* stream) {
+    BatchArgs<T> none = {};
+    return launch<T, false>(a, none, a.grid, a.tile_m, a.chunk_n, a.vec, i, parity, pdl, stream);
+}
+
+template <typename T>
+int launch_step_batch(const BatchArgs<T>& b, int i, int parity, bool pdl, void* stream) {
+    StepArgs<T> none = {};
+    return launch<T, true>(none, b, b.grid, b.tile_m, b.chunk_n, b.vec, i, parity, pdl, stream);
+}
+
+#define BTE_STEP_INSTANTIATE(T)                                                    \
+    template size_t step_smem_bytes<T>(int, int, int);                             \
+    template int step_block_threads<T>(int, int);                                  \
+    template int step_max_tile<T>(int);                                            \
+    template int step_kernel_configure<T>(int, int, int, int*);                    \
+    template int step_kernel_configure_batch<T>(int, int, int, int*);              \
+    template int launch_step<T>(const StepArgs<T>&, int, int, bool, void*);        \
+    template int launch_step_batch<T>(const BatchArgs<T>&, int, int, bool, void*);
 BTE_STEP_INSTANTIATE(float)
 BTE_STEP_INSTANTIATE(double)
 

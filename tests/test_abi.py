@@ -78,3 +78,32 @@ def test_workspace_size_covers_state():
     assert n64 >= 8 * p.cells * 8
     with pytest.raises(bte.BteError):
         bte.workspace_size(p, tile_m=30)
+
+
+@pytest.mark.parametrize("case", ["mixed_precision", "vec3", "fp64_vec4", "tile", "chunk",
+                                  "bad_point", "smem"])
+def test_batch_run_rejects_bad_input_on_host(case):
+    """bte_batch_run validates every point and option before any CUDA call."""
+    pts = [W.c1_fp64(), W.c1_fp64().replace(omega=2.0)]
+    kw = {}
+    if case == "mixed_precision":
+        pts[1] = pts[1].replace(precision=W.FP32_MIXED)
+    elif case == "vec3":
+        kw = dict(vec=3)
+    elif case == "fp64_vec4":
+        kw = dict(vec=4)
+    elif case == "tile":
+        kw = dict(tile_m=30)
+    elif case == "chunk":
+        kw = dict(chunk_n=2)
+    elif case == "bad_point":
+        pts[1] = pts[1].replace(m_points=2)
+    elif case == "smem":
+        kw = dict(tile_m=1024, chunk_n=4096)
+    with pytest.raises(bte.BteError) as e:
+        bte.batch_run(pts, **kw)
+    assert e.value.code == bte.EINVAL
+
+
+def test_batch_run_of_nothing_is_ok():
+    assert bte.batch_run([]) == []
