@@ -374,13 +374,229 @@ def run_ours(args):
     return 0
 
 
+SWEEP_DESC = ("batched sweep: seeded uniform E_dc in [0,6], E_omega in [0.01,1], omega in [0.5,6], "
+              "B in [0,6], mu in [0.5,10] (seed 1401); per-point n_max 20..200 and 201..2001 "
+              "phi_y points by the grid rule; dt=1e-3, 30 periods, last 10 averaged")
+
+
+def sweep_sample(args):
+    """The 4096-point sweep and the bounded sample of it one step solves:
+    every (4096 / n)-th point (the points are i.i.d. draws, so a stride is
+    an unbiased sample)."""
+    from paper_1401_6047_gb300 import workloads as W
+    prec = W.FP64 if args.precision == "fp64" else W.FP32_MIXED
+    pts = W.sweep_points(4096, precision=prec)
+    n = max(1, min(4096, args.sweep_sample))
+    stride = 4096 // n
+    return pts[::stride][:n], stride
+
+
+def sweep_launches(pts, max_batch, max_bytes, elem, tile, chunk, graph_len):
+    """Kernel launches of one bte_batch_run (same grouping rule as the library)."""
+    from paper_1401_6047_gb300 import bte
+    info = []
+    for p in pts:
+        _, P, K, _ = bte.time_grid(p)
+        info.append((K, P, p))
+    info.sort(key=lambda t: -t[0])
+    n, i = 0, 0
+    while i < len(info):
+        j, byt = i, 0
+        while j < len(info) and j - i < max_batch:
+            K, P, p = info[j]
+            ntx = -(-p.m_points // tile)
+            pitch = -(-(128 // elem + ntx * tile + 32 // elem) // 32) * 32
+            sb = 8 * (p.n_max + 1) * pitch * elem + 2 * (P + 2) * 8 + 4096
+            if j > i and byt + sb > max_bytes:
+                break
+            byt += sb
+            j += 1
+        Kmax = info[i][0]
+        L = min(graph_len, Kmax)
+        full = Kmax // L if L >= 2 else 0
+        left = Kmax - full * L
+        n += 3 * (j - i) + Kmax + full + (1 if left else 0)
+        i = j
+    return n
+
+
+def run_sweep(args):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_1401_6047_gb300 import bte
+
+    allpts, stride = sweep_sample(args)
+    # weak scaling: rank r solves every world-th point of the sample
+    pts = allpts[rank::world] if world > 1 else allpts
+    elem = 8 if args.precision == "fp64" else 4
+    vec = args.vec or (2 if elem == 8 else 4)
+    tile = args.tile_m or 64 * vec
+    chunk = args.chunk_n or 16
+    max_batch = args.max_batch or 1024
+    max_bytes = args.max_batch_bytes or (4 << 30)
+    cu = 0
+    for p in pts:
+        cu += p.cells * bte.time_grid(p)[2]
+    stream = torch.cuda.Stream(device=dev)
+    kw = dict(tile_m=tile, chunk_n=chunk, vec=vec, graph_steps=args.graph_steps,
+              max_batch=max_batch, max_batch_bytes=max_bytes, stream=stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        res = bte.batch_run(pts, **kw)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    evs = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record(stream)
+        res = bte.batch_run(pts, **kw)
+        e[1].record(stream)
+        evs.append(e)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    secs = total_ms * 1e-3
+    value = len(allpts) * args.steps / secs
+    bad = sum(1 for o in res if o.status != bte.OK)
+    peak, peak_kind = measured_peaks()
+    achieved = 8 * elem * cu * args.steps / (secs / 1 if world == 1 else secs) / 1e9
+    graph_len = args.graph_steps or 1024
+    launches = sweep_launches(pts, max_batch, max_bytes, elem, tile, chunk, graph_len)
+
+    # end to end: host parameter array in, host results out, through the C ABI
+    # (bte_batch_run allocates, uploads tables, runs, reads back and frees)
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bte.batch_run(pts, **{k: v for k, v in kw.items() if k != "stream"})
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = t.item()
+        e2e = {"value": len(allpts) / el, "unit": "points/s",
+               "h2d_bytes_per_step": len(pts) * 112, "d2h_bytes_per_step": len(pts) * 96}
+
+    # the plain single-instance GPU solver on a few of the same points
+    single = None
+    if rank == 0 and args.single_sample > 0:
+        sub = pts[:: max(1, len(pts) // args.single_sample)][: args.single_sample]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for p in sub:
+            bte.solve(p, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        cu_sub = sum(p.cells * bte.time_grid(p)[2] for p in sub)
+        # scale to the sample's mix by cell-updates
+        single = {"points_per_s": len(sub) / el * (cu_sub / len(sub)) / (cu / len(pts)),
+                  "cell_updates_per_s": cu_sub / el, "points": len(sub),
+                  "note": "bte_solve one point after another on the same stream; points/s "
+                          "scaled to the sample's mean cell-updates per point"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        p0 = pts[0].replace(precision=0)
+        v, cores, n, el = oracle_sample(p0, args.cpu_seconds)
+        cpu = {"value": v / (cu / len(pts)), "unit": "points/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n} steps of sweep point 0 ({p0.n_max + 1}x{p0.m_points}, FP64 "
+                         f"oracle, {el:.1f} s) = {v:.3e} cell-updates/s, divided by the "
+                         f"sample's mean {cu / len(pts):.3e} cell-updates per point"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if elem == 8 else "f32", "data": "synthetic",
+            "config": {"workload": "c4: " + SWEEP_DESC, "points_per_step": len(allpts),
+                       "sample": f"every {stride}th of the 4096 points",
+                       "cell_updates_per_step": cu * world, "cell_updates_per_s": cu * world * args.steps / secs,
+                       "precision": "fp64" if elem == 8 else "fp32 state, fp64 drive/reductions",
+                       "tile_m": tile, "chunk_n": chunk, "vec": vec, "max_batch": max_batch,
+                       "max_batch_bytes": max_bytes, "points_not_ok": bad,
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"points split over {world} rank(s)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": peak_kind + " hbm_gbs",
+                         "kernel": "fused_step_kernel (batched)",
+                         "note": "algorithmic bytes (32 B FP32 / 64 B FP64 per cell-update) "
+                                 "over the whole batch solve, so a lower bound for the kernel"},
+            "cpu_baseline": cpu, "single_instance_gpu": single, "e2e": e2e,
+            "gpu_launches": launches * args.steps, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_sweep_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1401_6047_gb300 import bte
+    oracle.build()
+    pts, stride = sweep_sample(args)
+    mean_cu = sum(p.cells * bte.time_grid(p)[2] for p in pts) / len(pts)
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    for i in range(args.warmup):
+        oracle_sample(pts[i % len(pts)].replace(precision=0), min(per_step, 5.0))
+    cus, secs, cores = 0.0, 0.0, 0
+    for i in range(args.steps):
+        p = pts[(7 * i) % len(pts)].replace(precision=0)
+        v, cores, n, el = oracle_sample(p, per_step)
+        cus += p.cells * n
+        secs += el
+    value = cus / secs / mean_cu
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "c4: " + SWEEP_DESC, "points_per_step": len(pts),
+                   "precision": "fp64 (oracle)"},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} bounded runs of sweep points; cell-updates/s "
+                                   f"divided by the mean {mean_cu:.3e} cell-updates per point"},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "table1"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "table1", "c4"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--tile-m", dest="tile_m", type=int, default=0)
     ap.add_argument("--chunk-n", dest="chunk_n", type=int, default=0)
@@ -391,9 +607,17 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--periods", type=float, default=0.0,
                     help="shorter run (drive periods) for profiling; 0 = the workload's")
+    ap.add_argument("--sweep-sample", dest="sweep_sample", type=int, default=256,
+                    help="c4: points of the 4096-point sweep solved per step")
+    ap.add_argument("--max-batch", dest="max_batch", type=int, default=0)
+    ap.add_argument("--max-batch-bytes", dest="max_batch_bytes", type=int, default=0)
+    ap.add_argument("--single-sample", dest="single_sample", type=int, default=8,
+                    help="c4: points solved one by one for the single-instance comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.config == "c4":
+        return run_sweep_reference(args) if args.impl == "reference" else run_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -209,7 +209,7 @@ BTE_API int bte_observe_noalloc(const bte_params* p, const void* a0_row, const v
 
 /* Options of bte_batch_run (zero fields take the defaults given). */
 typedef struct bte_batch_opts {
-    int32_t tile_m;          /* phi_y columns per work item (0: 32 * vec)             */
+    int32_t tile_m;          /* phi_y columns per work item (0: 64 * vec)             */
     int32_t chunk_n;         /* harmonics per work item (0: 16)                       */
     int32_t vec;             /* columns per thread, 2 or 4 (0: 4 FP32, 2 FP64)        */
     int32_t graph_steps;     /* steps per captured CUDA graph (0: 1024)               */

@@ -88,6 +88,7 @@ struct BatchInst {
 template <typename T>
 struct BatchArgs {
     const BatchInst<T>* inst;
+    const int* item_inst; /* [items] instance of each work item                  */
     int ninst, items;     /* instances; total work items                         */
     const long long* base;/* common step counter                                 */
     int* err;

@@ -171,8 +171,8 @@ struct View {
     T Ews, Ewe, Efs, Efe, h, hh, nu, xi, cc;
 };
 
-/* Instance of item q: single-instance launches use A; batched ones search
- * the records by first item index. */
+/* Instance of item q: single-instance launches use A; batched ones look the
+ * instance up in the item -> instance table. */
 template <typename T, bool BATCH>
 __device__ __forceinline__ void make_view(View<T>& v, int q, const StepArgs<T>& A,
                                           const BatchArgs<T>& Bt, long long kbase, int cur,
@@ -212,12 +212,7 @@ __device__ __forceinline__ void make_view(View<T>& v, int q, const StepArgs<T>& 
             v.cc = A.c;
         }
     } else {
-        int lo = 0, hi = Bt.ninst - 1; /* last instance with item0 <= q */
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (Bt.inst[mid].item0 <= q) lo = mid;
-            else hi = mid - 1;
-        }
+        const int lo = __ldg(Bt.item_inst + q);
         const BatchInst<T>& I = Bt.inst[lo];
         v.inst = lo;
         v.q0 = I.item0;

@@ -124,7 +124,7 @@ def test_batch_reports_unstable_point_and_keeps_the_rest():
     res = bte.batch_run(pts, check=False)
     assert res[1].status == bte.EUNSTABLE
     for p, o in zip(pts[:1] + pts[2:], res[:1] + res[2:]):
-        r = bte.solve(p, tile_m=64, chunk_n=16)
+        r = bte.solve(p, tile_m=128, chunk_n=16)
         _same_obs(o, r)
 
 
