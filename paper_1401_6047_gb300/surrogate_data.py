@@ -1,0 +1,49 @@
+"""Training and held-out data of the MLP surrogate: seeded points of the
+sweep box, each solved by the batched CUDA solver (``bte_batch_run``) under
+the surrogate run protocol (``workloads.surrogate_params``).
+
+Usage: python -m paper_1401_6047_gb300.surrogate_data OUT.npz N SEED [CHUNK]
+
+Writes x [N, 5] (E_dc, E_omega, omega, B, mu) and y [N, 2] (absorption,
+time-averaged drift velocity) as float64, plus a per-point status; the file
+is rewritten after every chunk so that an interrupted run keeps its work.
+"""
+from __future__ import annotations
+
+import os
+import sys
+import time
+
+import numpy as np
+
+from . import bte
+from . import workloads as W
+
+
+def generate(path: str, n: int, seed: int, chunk: int = 4096, precision: int = W.FP32_MIXED):
+    X = W.sweep_matrix(n, seed)
+    Y = np.full((n, 2), np.nan)
+    S = np.full(n, -99, dtype=np.int32)
+    done = 0
+    if os.path.exists(path):
+        d = np.load(path)
+        if d["x"].shape == X.shape and np.array_equal(d["x"], X):
+            Y, S, done = d["y"].copy(), d["status"].copy(), int(d["done"])
+    t0 = time.time()
+    while done < n:
+        hi = min(n, done + chunk)
+        pts = [W.surrogate_params(x, precision) for x in X[done:hi]]
+        res = bte.batch_run(pts, check=False)
+        Y[done:hi, 0] = [o.absorption for o in res]
+        Y[done:hi, 1] = [o.v_dc_avg for o in res]
+        S[done:hi] = [o.status for o in res]
+        done = hi
+        np.savez(path, x=X, y=Y, status=S, done=done, seed=seed)
+        print(f"{done}/{n} points, {time.time() - t0:.1f} s", flush=True)
+    return X, Y, S
+
+
+if __name__ == "__main__":
+    out, n, seed = sys.argv[1], int(sys.argv[2]), int(sys.argv[3])
+    chunk = int(sys.argv[4]) if len(sys.argv) > 4 else 4096
+    generate(out, n, seed, chunk)

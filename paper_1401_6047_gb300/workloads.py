@@ -145,3 +145,28 @@ def random_state(p: Params, seed: int, scale: float = 1.0, parity: int | None = 
         mask = ((n + m) % 2) == parity
         arrs = [np.where(mask, x, 0.0) for x in arrs]
     return arrs
+
+
+# Surrogate workload: the points the MLP surrogate is trained on and replaces
+# the solver for.  Same box and grid rule as the sweep; the run length is
+# what the periodic steady state needs rather than a fixed 30 periods: the
+# collision term damps any deviation from the periodic state as exp(-t)
+# along the (measure-preserving) characteristics, so after t >= 16 the
+# transient is below 1.2e-7 of its start, and the window average over one
+# whole period of a periodic signal equals the average over any number.
+SURROGATE_T_TRANSIENT = 16.0
+SURROGATE_TRAIN_SEED = 6047
+SURROGATE_HELDOUT_SEED = 2015
+SURROGATE_INFER_SEED = 2014
+
+
+def surrogate_params(x, precision: int = FP32_MIXED) -> Params:
+    """Solver parameters of one surrogate input x = (E_dc, E_omega, omega, B, mu):
+    the sweep's grid rule, dt = 1e-3, ceil(16 omega / 2 pi) + 1 periods with
+    the last one averaged."""
+    E_dc, E_omega, omega, B, mu = (float(v) for v in x)
+    n_max, m_points, L = sweep_grid_rule(mu, B)
+    periods = math.ceil(SURROGATE_T_TRANSIENT * omega / (2.0 * math.pi)) + 1
+    return Params(E_dc=E_dc, E_omega=E_omega, omega=omega, B=B, mu=mu, n_max=n_max,
+                  m_points=m_points, phiy_min=-L, phiy_max=L, dt=1e-3, periods=float(periods),
+                  avg_window=1.0, precision=precision)
