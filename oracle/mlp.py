@@ -74,15 +74,31 @@ def normalise_x(x, lo, hi):
     return 2.0 * (x - lo) / (hi - lo) - 1.0
 
 
-def forward(p: dict, xh: np.ndarray):
+def bf16(a):
+    """Round to the nearest bfloat16 (ties to even), returned as float64:
+    the float32 value's top 16 bits after adding 0x7fff plus the lowest kept
+    bit (finite inputs)."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _id(a):
+    return a
+
+
+def forward(p: dict, xh: np.ndarray, mixed: bool = False):
     """Standardised outputs yh [B, 2] and the pre-activations / activations
-    the backward pass needs."""
+    the backward pass needs.  mixed = True rounds what the tensor-core
+    layers and the output layer read to bfloat16: the hidden activations
+    h1, h2, h3 and the weights W2, W3 (all other arithmetic stays float64)."""
+    r = bf16 if mixed else _id
     z1 = xh @ p["W1"].T + p["b1"]
-    h1 = silu(z1)
-    z2 = h1 @ p["W2"].T + p["b2"]
-    h2 = silu(z2)
-    z3 = h2 @ p["W3"].T + p["b3"]
-    h3 = silu(z3)
+    h1 = r(silu(z1))
+    z2 = h1 @ r(p["W2"]).T + p["b2"]
+    h2 = r(silu(z2))
+    z3 = h2 @ r(p["W3"]).T + p["b3"]
+    h3 = r(silu(z3))
     yh = h3 @ p["W4"].T + p["b4"]
     return yh, dict(xh=xh, z1=z1, h1=h1, z2=z2, h2=h2, z3=z3, h3=h3)
 
@@ -92,28 +108,31 @@ def loss(yh, th):
     return 0.5 * np.sum((yh - th) ** 2) / B
 
 
-def backward(p: dict, cache: dict, dyh: np.ndarray) -> dict:
+def backward(p: dict, cache: dict, dyh: np.ndarray, mixed: bool = False) -> dict:
     """Gradients of every parameter given dL/dyh [B, 2] (chain rule, layer
-    by layer from the output)."""
+    by layer from the output).  mixed = True also rounds the back-propagated
+    pre-activation gradients dz3, dz2, dz1 and the weights W2, W3 to
+    bfloat16, as the tensor-core path stores and reads them."""
+    r = bf16 if mixed else _id
     g = {}
     g["W4"] = dyh.T @ cache["h3"]
     g["b4"] = dyh.sum(axis=0)
-    dz3 = (dyh @ p["W4"]) * silu_grad(cache["z3"])
+    dz3 = r((dyh @ p["W4"]) * silu_grad(cache["z3"]))
     g["W3"] = dz3.T @ cache["h2"]
     g["b3"] = dz3.sum(axis=0)
-    dz2 = (dz3 @ p["W3"]) * silu_grad(cache["z2"])
+    dz2 = r((dz3 @ r(p["W3"])) * silu_grad(cache["z2"]))
     g["W2"] = dz2.T @ cache["h1"]
     g["b2"] = dz2.sum(axis=0)
-    dz1 = (dz2 @ p["W2"]) * silu_grad(cache["z1"])
+    dz1 = r((dz2 @ r(p["W2"])) * silu_grad(cache["z1"]))
     g["W1"] = dz1.T @ cache["xh"]
     g["b1"] = dz1.sum(axis=0)
     return g
 
 
-def loss_and_grad(p: dict, xh: np.ndarray, th: np.ndarray):
-    yh, cache = forward(p, xh)
+def loss_and_grad(p: dict, xh: np.ndarray, th: np.ndarray, mixed: bool = False):
+    yh, cache = forward(p, xh, mixed)
     B = xh.shape[0]
-    return loss(yh, th), backward(p, cache, (yh - th) / B)
+    return loss(yh, th), backward(p, cache, (yh - th) / B, mixed)
 
 
 def adam(flat, grad, m, v, t: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
@@ -139,13 +158,13 @@ def init_member(seed: int, H: int = 256) -> np.ndarray:
     return pack(p, H)
 
 
-def ensemble(flats, x, lo, hi, y_mean, y_std, H: int = 256):
+def ensemble(flats, x, lo, hi, y_mean, y_std, H: int = 256, mixed: bool = False):
     """Mean and population standard deviation over members of the
     de-standardised outputs, [B, 2] each."""
     xh = normalise_x(x, lo, hi)
     ys = []
     for f in flats:
-        yh, _ = forward(unpack(f, H), xh)
+        yh, _ = forward(unpack(f, H), xh, mixed)
         ys.append(yh * np.asarray(y_std) + np.asarray(y_mean))
     ys = np.stack(ys)
     mean = ys.mean(axis=0)

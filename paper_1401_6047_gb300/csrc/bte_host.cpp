@@ -823,6 +823,14 @@ int run_batch(const bte_params* p, std::vector<BatchPoint>& pts, size_t first, s
 
 }  // namespace
 
+namespace bte {
+/* Sets the thread's last-error message for other translation units. */
+int report_error(int code, const char* msg) {
+    g_err = msg ? msg : "";
+    return code;
+}
+}  // namespace bte
+
 extern "C" {
 
 const char* bte_last_error(void) { return g_err.c_str(); }

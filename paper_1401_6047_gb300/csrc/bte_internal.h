@@ -139,6 +139,8 @@ int launch_observe(const T* a_w, const T* b_w, int M, int pitch, double vscale,
                    void* stream);
 int launch_advance_base(long long* base, long long by, void* stream);
 int launch_finalize(const FinalArgs& a, void* stream);
+/* Sets the calling thread's bte_last_error() message; returns code. */
+int report_error(int code, const char* msg);
 template <typename T>
 size_t step_smem_bytes(int tile_m, int chunk_n, int vec);
 template <typename T>

@@ -19,6 +19,23 @@ import numpy as np
 from . import bte
 from . import workloads as W
 
+DATA_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
+FILES = {"train": "surrogate_train.npz", "heldout": "surrogate_heldout.npz"}
+
+# training schedule of the shipped ensemble (Adam, cosine decay of lr)
+TRAINING = dict(epochs=200, batch=1024, lr=2e-3, lr_min=2e-5, seed=0)
+
+
+def load(name: str):
+    """(x, y) of a data file, points the solver reported OK only; None when
+    the file is absent."""
+    path = os.path.join(DATA_DIR, FILES[name])
+    if not os.path.exists(path):
+        return None
+    d = np.load(path)
+    ok = (d["status"] == bte.OK) & np.all(np.isfinite(d["y"]), axis=1)
+    return d["x"][ok], d["y"][ok]
+
 
 def generate(path: str, n: int, seed: int, chunk: int = 4096, precision: int = W.FP32_MIXED):
     X = W.sweep_matrix(n, seed)

@@ -1,0 +1,72 @@
+"""What the trained surrogate gains over the solver alone.
+
+An 8-member ensemble is trained on the committed training set (points of
+the sweep box solved by the batched solver under the surrogate protocol)
+and judged on held-out points solved the same way.  The surrogate with
+solver fallback (threshold 1e-3 on the ensemble standard deviation) must
+(1) keep the points it answers itself close to the solver, and (2) finish
+a held-out sample faster than the solver alone.
+"""
+import os
+import time
+
+import numpy as np
+import pytest
+
+from paper_1401_6047_gb300 import bte
+from paper_1401_6047_gb300 import surrogate as S
+from paper_1401_6047_gb300 import surrogate_data as D
+
+pytestmark = pytest.mark.gpu
+
+THRESHOLD = 1e-3
+
+
+@pytest.fixture(scope="module")
+def trained():
+    tr = D.load("train")
+    ho = D.load("heldout")
+    if tr is None or ho is None:
+        pytest.skip("surrogate data files are not present")
+    x, y = tr
+    sur = S.Surrogate(y.mean(axis=0), y.std(axis=0), members=8, batch_capacity=16384)
+    sur.set_params(S.init_params(8, seed=0))
+    hist = sur.fit(x, y, **D.TRAINING)
+    yield sur, hist, ho
+    sur.close()
+
+
+def test_training_converges(trained):
+    sur, hist, _ = trained
+    assert hist[-1] < hist[0] / 50
+
+
+def test_accepted_points_match_the_solver(trained):
+    sur, _, (x, y) = trained
+    mean, std, mask = sur.predict(x, threshold=THRESHOLD)
+    acc = ~mask
+    err = np.abs(mean - y).max(axis=1)
+    assert acc.mean() > 0.2, acc.mean()
+    # the ensemble spread bounds the error of the points it keeps: 99% within
+    # 5 x threshold, all within 50 x threshold
+    assert np.quantile(err[acc], 0.99) <= 5 * THRESHOLD
+    assert err[acc].max() <= 50 * THRESHOLD
+
+
+def test_hybrid_is_faster_than_the_solver_alone(trained):
+    sur, _, (x, y) = trained
+    sample = x[::16][:256]
+    pts = [S.protocol(xi) for xi in sample]
+    t0 = time.perf_counter()
+    ref = bte.batch_run(pts)
+    t_solver = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    yh, solved, status = sur.hybrid(sample, threshold=THRESHOLD)
+    t_hybrid = time.perf_counter() - t0
+    frac = solved.mean()
+    assert np.all(status == bte.OK)
+    # solved points carry the solver's own values
+    for i in np.nonzero(solved)[0]:
+        assert yh[i, 0] == ref[i].absorption and yh[i, 1] == ref[i].v_dc_avg
+    # the saving follows the fraction the ensemble answers itself
+    assert t_hybrid < t_solver * (frac + 0.25), (t_hybrid, t_solver, frac)

@@ -142,3 +142,32 @@ def test_planted_mistake_is_caught_by_finite_differences(monkeypatch):
     monkeypatch.undo()
     _, g_ok = mlp.loss_and_grad(mlp.unpack(flat, H), xh, th)
     assert np.linalg.norm(mlp.pack(g, H) - mlp.pack(g_ok, H)) > 1e-3 * np.linalg.norm(mlp.pack(g_ok, H))
+
+
+def test_bf16_rounding_matches_torch_and_ties_to_even():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(14)
+    a = np.concatenate([rng.normal(0, 1, 5000), rng.normal(0, 1e-3, 1000),
+                        rng.uniform(-300, 300, 1000), [0.0, -0.0, 1.0, 2.0 ** -130]])
+    ref = torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.bf16(a), ref)
+    # 1 + 2^-8 lies halfway between 1 and 1 + 2^-7: ties go to the even 1.0;
+    # 1 + 3 * 2^-8 lies halfway between 1 + 2^-7 and 1 + 2^-6: even is 1 + 2^-6
+    assert mlp.bf16(1 + 2.0 ** -8) == 1.0
+    assert mlp.bf16(1 + 3 * 2.0 ** -8) == 1 + 2.0 ** -6
+
+
+def test_mixed_precision_network_stays_close_to_fp64():
+    """The bfloat16-rounded network differs from the FP64 one by the
+    bfloat16 unit roundoff (2^-9 relative) accumulated over three layers."""
+    flat = _net(15, H=64, scale=0.2)
+    xh, th = _batch(16, B=33)
+    p = mlp.unpack(flat, 64)
+    y64, _ = mlp.forward(p, xh)
+    y16, _ = mlp.forward(p, xh, mixed=True)
+    assert np.max(np.abs(y16 - y64)) <= 2e-2 * np.max(np.abs(y64))
+    assert np.max(np.abs(y16 - y64)) > 0
+    _, g64 = mlp.loss_and_grad(p, xh, th)
+    _, g16 = mlp.loss_and_grad(p, xh, th, mixed=True)
+    for k in g64:
+        assert np.linalg.norm(g16[k] - g64[k]) <= 3e-2 * np.linalg.norm(g64[k]), k
