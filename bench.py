@@ -590,13 +590,228 @@ def run_sweep_reference(args):
     return 0
 
 
+SUR_DESC = ("learned surrogate: 8-member ensemble of MLP 5-256-256-256-2 (SiLU), BF16 tensor-core "
+            "layers with FP32 accumulation, trained on 32,768 sweep-box points solved by the "
+            "batched solver; inference on 1M seeded points (seed 2014) of the same box, solver "
+            "fallback where the ensemble std exceeds 1e-3")
+
+
+def sur_flops_per_point(members=8, H=256):
+    """Multiply-adds x 2 of one forward pass of every member."""
+    return members * 2 * (5 * H + 2 * H * H + 2 * H)
+
+
+def run_surrogate(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_1401_6047_gb300 import bte
+    from paper_1401_6047_gb300 import surrogate as S
+    from paper_1401_6047_gb300 import surrogate_data as D
+    from paper_1401_6047_gb300 import workloads as W
+
+    x_tr, y_tr = D.load("train")
+    x_ho, y_ho = D.load("heldout")
+    stream = torch.cuda.Stream(device=dev)
+    sur = S.Surrogate(y_tr.mean(axis=0), y_tr.std(axis=0), members=8, batch_capacity=65536,
+                      stream=stream.cuda_stream)
+    sur.set_params(S.init_params(8, seed=0))
+    t0 = time.perf_counter()
+    hist = sur.fit(x_tr, y_tr, **D.TRAINING)
+    train_s = time.perf_counter() - t0
+
+    n = args.sur_points
+    xs = W.sweep_matrix(n * world, W.SURROGATE_INFER_SEED)[rank * n:(rank + 1) * n]
+    xd = torch.from_numpy(xs.astype(np.float32)).to(dev)
+    md = torch.empty((n, 2), device=dev)
+    sd = torch.empty((n, 2), device=dev)
+    kd = torch.empty(n, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        sur.predict_device(xd.data_ptr(), n, md.data_ptr(), sd.data_ptr(), kd.data_ptr(), 1e-3)
+
+    for _ in range(args.warmup):
+        step()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    evs = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record(stream)
+        step()
+        e[1].record(stream)
+        evs.append(e)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    secs = total_ms * 1e-3
+    value = world * n * args.steps / secs
+    frac_solver = float(kd.float().mean().item())
+    flops = sur_flops_per_point() * n
+    tflops = flops * args.steps / secs / 1e12
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+
+    # end to end: host inputs in, host mean / std / mask out
+    e2e = None
+    if not args.no_e2e:
+        x32 = np.ascontiguousarray(xs, dtype=np.float32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sur.predict(x32, threshold=1e-3)
+        el = time.perf_counter() - t0
+        e2e = {"value": world * n / el, "unit": "points/s", "h2d_bytes_per_step": int(n * 20),
+               "d2h_bytes_per_step": int(n * 17)}
+
+    # accuracy on held-out solver results, and the hybrid against the solver alone
+    mean, std, mask = sur.predict(x_ho, threshold=1e-3)
+    err = np.abs(mean - y_ho).max(axis=1)
+    acc = ~mask
+    hybrid = None
+    if rank == 0 and args.hybrid_sample > 0:
+        sample = x_ho[:: max(1, len(x_ho) // args.hybrid_sample)][: args.hybrid_sample]
+        pts = [S.protocol(xi) for xi in sample]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bte.batch_run(pts)
+        t_solver = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        yh, solved, _ = sur.hybrid(sample, threshold=1e-3)
+        t_hybrid = time.perf_counter() - t0
+        hybrid = {"points": len(sample), "hybrid_points_per_s": len(sample) / t_hybrid,
+                  "solver_only_points_per_s": len(sample) / t_solver,
+                  "fraction_solved": float(solved.mean())}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import mlp
+        P = sur.get_params().astype(np.float64)
+        lo, hi = S.box_bounds()
+        m0 = 2048
+        t0 = time.perf_counter()
+        cnt = 0
+        while time.perf_counter() - t0 < args.cpu_seconds:
+            mlp.ensemble(list(P), xs[cnt % (n - m0):cnt % (n - m0) + m0], lo, hi,
+                         y_tr.mean(axis=0), y_tr.std(axis=0))
+            cnt += m0
+        el = time.perf_counter() - t0
+        cpu = {"value": cnt / el, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{cnt} points through the FP64 numpy ensemble ({el:.1f} s; numpy's "
+                         f"BLAS threads)"}
+    sur.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": "c5: " + SUR_DESC, "points_per_step": n * world,
+                       "train_seconds": train_s, "train_final_loss": hist[-1],
+                       "fraction_to_solver": frac_solver,
+                       "heldout": {"points": int(len(x_ho)), "accepted": float(acc.mean()),
+                                   "err_p50_accepted": float(np.median(err[acc])) if acc.any() else None,
+                                   "err_p99_accepted": float(np.quantile(err[acc], 0.99)) if acc.any() else None,
+                                   "err_max_accepted": float(err[acc].max()) if acc.any() else None,
+                                   "err_p50_all": float(np.median(err))},
+                       "hybrid": hybrid,
+                       "l2": "flushed (256 MB write) before every timed step; inputs 20 MB"},
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tflops / peak, "traffic": None,
+                         "peak_source": "measured bf16_tflops (cuBLAS burst)",
+                         "kernel": "whole ensemble forward (5 kernels per 65,536-point chunk)",
+                         "flops_per_point": sur_flops_per_point()},
+            "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 5 * (-(-n // 65536)) * args.steps, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_surrogate_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import mlp
+    from paper_1401_6047_gb300 import surrogate as S
+    from paper_1401_6047_gb300 import surrogate_data as D
+    from paper_1401_6047_gb300 import workloads as W
+    x_tr, y_tr = D.load("train")
+    P = [mlp.init_member(m) for m in range(8)]
+    lo, hi = S.box_bounds()
+    xs = W.sweep_matrix(65536, W.SURROGATE_INFER_SEED)
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    m0 = 2048
+
+    def sample(limit):
+        t0 = time.perf_counter()
+        cnt = 0
+        while time.perf_counter() - t0 < limit:
+            mlp.ensemble(P, xs[cnt % 60000:cnt % 60000 + m0], lo, hi, y_tr.mean(axis=0),
+                         y_tr.std(axis=0))
+            cnt += m0
+        return cnt, time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        sample(min(per_step, 3.0))
+    cnt, el = 0, 0.0
+    for _ in range(args.steps):
+        c, e = sample(per_step)
+        cnt += c
+        el += e
+    value = cnt / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "c5: " + SUR_DESC, "precision": "fp64 (oracle)"},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": os.cpu_count(),
+                         "kind": "oracle",
+                         "sample": f"{cnt} points through the FP64 numpy ensemble"},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "table1", "c4"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "table1", "c4", "c5"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--tile-m", dest="tile_m", type=int, default=0)
     ap.add_argument("--chunk-n", dest="chunk_n", type=int, default=0)
@@ -613,9 +828,15 @@ def main():
     ap.add_argument("--max-batch-bytes", dest="max_batch_bytes", type=int, default=0)
     ap.add_argument("--single-sample", dest="single_sample", type=int, default=8,
                     help="c4: points solved one by one for the single-instance comparison")
+    ap.add_argument("--sur-points", dest="sur_points", type=int, default=1_000_000,
+                    help="c5: points per inference step")
+    ap.add_argument("--hybrid-sample", dest="hybrid_sample", type=int, default=256,
+                    help="c5: held-out points timed through the surrogate with solver fallback")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.config == "c5":
+        return run_surrogate_reference(args) if args.impl == "reference" else run_surrogate(args)
     if args.config == "c4":
         return run_sweep_reference(args) if args.impl == "reference" else run_sweep(args)
     if args.impl == "reference":
