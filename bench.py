@@ -444,7 +444,8 @@ def run_sweep(args):
         cu += p.cells * bte.time_grid(p)[2]
     stream = torch.cuda.Stream(device=dev)
     kw = dict(tile_m=tile, chunk_n=chunk, vec=vec, graph_steps=args.graph_steps,
-              max_batch=max_batch, max_batch_bytes=max_bytes, stream=stream.cuda_stream)
+              max_batch=max_batch, max_batch_bytes=max_bytes, stream=stream.cuda_stream,
+              resident=args.resident, resident_smem=args.resident_smem)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         res = bte.batch_run(pts, **kw)
@@ -825,6 +826,10 @@ def main():
     ap.add_argument("--sweep-sample", dest="sweep_sample", type=int, default=256,
                     help="c4: points of the 4096-point sweep solved per step")
     ap.add_argument("--max-batch", dest="max_batch", type=int, default=0)
+    ap.add_argument("--resident", type=int, default=0,
+                    help="c4: 0 on chip where a point fits, 1 never, 2 only")
+    ap.add_argument("--resident-smem", dest="resident_smem", type=int, default=0,
+                    help="c4: shared memory per CTA for on-chip points (bytes)")
     ap.add_argument("--max-batch-bytes", dest="max_batch_bytes", type=int, default=0)
     ap.add_argument("--single-sample", dest="single_sample", type=int, default=8,
                     help="c4: points solved one by one for the single-instance comparison")

@@ -214,21 +214,30 @@ typedef struct bte_batch_opts {
     int32_t vec;             /* columns per thread, 2 or 4 (0: 4 FP32, 2 FP64)        */
     int32_t graph_steps;     /* steps per captured CUDA graph (0: 1024)               */
     int32_t max_batch;       /* parameter points advanced together (0: 1024)          */
-    int32_t reserved;
+    int32_t resident;        /* 0: on chip where a point fits, 1: never, 2: only      */
     int64_t max_batch_bytes; /* device bytes one batch may hold (0: 4 GiB)            */
     void* stream;            /* cudaStream_t to queue on (NULL: a private stream)     */
+    int32_t resident_smem;   /* shared memory per CTA for on-chip points, bytes
+                                (0: 113,664, two CTAs per SM; at most 232,448)       */
+    int32_t reserved;        /* must be 0                                             */
 } bte_batch_opts;
 
 /* Full solve (Sec. 3 scheme from the Sec. 2 initial state, window averages
  * of Eq. absorption_def) of n independent parameter points p[0..n-1], as a
  * parameter sweep of the kind behind the paper's absorption and drift maps
  * (Sec. 4).  All points must share one precision; each keeps its own grid,
- * time step and run length.  Points are grouped into batches (longest runs
- * first, at most max_batch points and about max_batch_bytes of device
- * memory each); the points of a batch advance in lock-step, one fused
- * launch per time step covering every point's tiles, so a batch of small
- * grids fills the GPU where one small grid cannot.  A point whose run is
- * over is skipped by later launches of its batch.  out[i] receives the
+ * time step and run length.  Two tiers:
+ *   on chip: a point whose four grid arrays fit the shared memory of a
+ *     cluster of C = 1, 2, 4, 8 or 16 CTAs (resident_smem bytes each) is
+ *     run start to end by one cluster with the state held in shared
+ *     memory; clusters take points from a queue, longest first;
+ *   streamed: the other points are grouped into batches (longest runs
+ *     first, at most max_batch points and about max_batch_bytes of device
+ *     memory each) that advance in lock-step, one fused launch per time
+ *     step covering every point's tiles; a point whose run is over is
+ *     skipped by later launches of its batch.
+ * Both give the same per-cell arithmetic; the per-step sums over phi_y are
+ * added in different orders.  out[i] receives the
  * final observables of p[i] exactly as bte_observables reports them after
  * bte_run (absorption NaN when omega == 0), with a per-point status
  * (BTE_OK, BTE_EUNSTABLE, BTE_ETIMEOUT).  Returns BTE_OK when every point

@@ -57,8 +57,9 @@ class bte_tuning(ctypes.Structure):
 class bte_batch_opts(ctypes.Structure):
     _fields_ = [("tile_m", ctypes.c_int32), ("chunk_n", ctypes.c_int32), ("vec", ctypes.c_int32),
                 ("graph_steps", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("max_batch_bytes", ctypes.c_int64),
-                ("stream", ctypes.c_void_p)]
+                ("resident", ctypes.c_int32), ("max_batch_bytes", ctypes.c_int64),
+                ("stream", ctypes.c_void_p), ("resident_smem", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -293,17 +294,20 @@ def _obs(o: bte_obs) -> Observables:
 
 def batch_run(points, tile_m: int = 0, chunk_n: int = 0, vec: int = 0, graph_steps: int = 0,
               max_batch: int = 0, max_batch_bytes: int = 0, stream: int = 0,
+              resident: int = 0, resident_smem: int = 0,
               check: bool = True) -> list[Observables]:
     """Full solves of many parameter points (``bte_batch_run``); returns one
-    ``Observables`` per point, in order.  With ``check`` a non-OK overall
-    status raises; without it the per-point ``status`` fields tell."""
+    ``Observables`` per point, in order.  ``resident``: 0 on chip where a
+    point fits, 1 never, 2 only.  With ``check`` a non-OK overall status
+    raises; without it the per-point ``status`` fields tell."""
     pts = list(points)
     n = len(pts)
     arr = (bte_params * max(n, 1))(*[to_params(q) for q in pts])
     out = (bte_obs * max(n, 1))()
     o = bte_batch_opts()
     o.tile_m, o.chunk_n, o.vec, o.graph_steps = int(tile_m), int(chunk_n), int(vec), int(graph_steps)
-    o.max_batch, o.reserved, o.max_batch_bytes = int(max_batch), 0, int(max_batch_bytes)
+    o.max_batch, o.resident, o.max_batch_bytes = int(max_batch), int(resident), int(max_batch_bytes)
+    o.resident_smem, o.reserved = int(resident_smem), 0
     o.stream = ctypes.c_void_p(stream or None)
     rc = lib().bte_batch_run(arr, n, out, ctypes.byref(o))
     if check:

@@ -523,6 +523,7 @@ namespace {
 
 struct BatchPoint {
     int idx; /* position in the caller's array */
+    int resC; /* CTAs per cluster of the on-chip tier, 0: streamed */
     TimeGrid tg;
     int N1, M1, ntx, nty, pitch, items;
     double dphi;
@@ -534,11 +535,12 @@ struct BatchPoint {
 
 constexpr int kAcc = 8; /* per-instance accumulators, see BatchInst::acc */
 
-/* Runs points [first, last) of `pts` as one batch advancing in lock-step. */
+/* Runs points [first, last) of `pts` as one batch: advancing in lock-step,
+ * or (resident) on chip, one cluster of pts[i].resC CTAs per point. */
 template <typename T>
 int run_batch(const bte_params* p, std::vector<BatchPoint>& pts, size_t first, size_t last,
-              int tile, int chunk, int vec, int graph_len, cudaStream_t st, cudaStream_t cap,
-              bte_obs* out) {
+              int tile, int chunk, int vec, int graph_len, bool resident, cudaStream_t st,
+              cudaStream_t cap, bte_obs* out) {
     const int elem = (int)sizeof(T);
     const int G = 128 / elem, Hp = 32 / elem;
     /* layout: [all states][all tables, accumulators][records][counter, error] */
@@ -550,7 +552,7 @@ int run_batch(const bte_params* p, std::vector<BatchPoint>& pts, size_t first, s
         b.pitch = (int)align_up((size_t)(G + b.ntx * tile + Hp), 32);
         b.state_bytes = align_up((size_t)b.N1 * b.pitch * elem, 256);
         b.state_off = o;
-        o += 8 * b.state_bytes;
+        o += (resident ? 4 : 8) * b.state_bytes; /* on chip: no ping-pong set */
         b.items = b.ntx * b.nty;
         items += b.items;
         Kmax = std::max(Kmax, b.tg.K);
@@ -626,10 +628,11 @@ int run_batch(const bte_params* p, std::vector<BatchPoint>& pts, size_t first, s
         unsigned char* tb = mem + b.tab_off;
         bte::BatchInst<T>& R = rec[i - first];
         for (int s = 0; s < 2; ++s) {
-            R.a_w[s] = reinterpret_cast<T*>(mem + b.state_off + (4 * s + 0) * b.state_bytes);
-            R.b_w[s] = reinterpret_cast<T*>(mem + b.state_off + (4 * s + 1) * b.state_bytes);
-            R.a_f[s] = reinterpret_cast<T*>(mem + b.state_off + (4 * s + 2) * b.state_bytes);
-            R.b_f[s] = reinterpret_cast<T*>(mem + b.state_off + (4 * s + 3) * b.state_bytes);
+            const int ss = resident ? 0 : s;
+            R.a_w[s] = reinterpret_cast<T*>(mem + b.state_off + (4 * ss + 0) * b.state_bytes);
+            R.b_w[s] = reinterpret_cast<T*>(mem + b.state_off + (4 * ss + 1) * b.state_bytes);
+            R.a_f[s] = reinterpret_cast<T*>(mem + b.state_off + (4 * ss + 2) * b.state_bytes);
+            R.b_f[s] = reinterpret_cast<T*>(mem + b.state_off + (4 * ss + 3) * b.state_bytes);
         }
         R.row_a0 = reinterpret_cast<const T*>(tb + b.o_row);
         R.col_g = reinterpret_cast<const T*>(tb + b.o_colg);
@@ -728,6 +731,106 @@ int run_batch(const bte_params* p, std::vector<BatchPoint>& pts, size_t first, s
     ba.tile_m = tile;
     ba.chunk_n = chunk;
     ba.vec = vec;
+    if (resident) {
+        /* on chip: one persistent launch per cluster size, all launches
+         * concurrent (each on its own stream, so the CTAs that one launch
+         * frees at its end go to the others); within a launch, clusters take
+         * points from a queue, costliest first (cells x steps) */
+        std::vector<int> order(n);
+        for (size_t i = 0; i < n; ++i) order[i] = (int)i;
+        std::sort(order.begin(), order.end(), [&](int x, int y) {
+            const BatchPoint& a = pts[first + x];
+            const BatchPoint& b = pts[first + y];
+            if (a.resC != b.resC) return a.resC > b.resC;
+            const double ca = (double)a.N1 * a.M1 * a.tg.K, cb = (double)b.N1 * b.M1 * b.tg.K;
+            return ca != cb ? ca > cb : x < y;
+        });
+        /* the item table is not used on this path: its space holds the order */
+        if (items < (int)n) {
+            rc = fail(BTE_ECUDA, "internal: order table too small");
+            cleanup();
+            return rc;
+        }
+        BCU(cudaMemcpyAsync(mem + map_off, order.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+        struct Launch {
+            int C, begin, count;
+            size_t smem, arrays;
+            double longest;
+        };
+        std::vector<Launch> launches;
+        for (size_t q = 0; q < n;) {
+            Launch L{pts[first + order[q]].resC, (int)q, 0, 0, 0, 0.0};
+            while (q < n && pts[first + order[q]].resC == L.C) {
+                const BatchPoint& b = pts[first + order[q]];
+                size_t ab = 0;
+                L.smem = std::max(L.smem, bte::resident_smem_bytes<T>(b.N1 - 1, b.M1 - 1, L.C, &ab));
+                L.arrays = std::max(L.arrays, ab);
+                L.longest = std::max(L.longest, (double)b.tg.K * b.N1 * b.M1 / L.C);
+                ++L.count;
+                ++q;
+            }
+            launches.push_back(L);
+        }
+        /* the launch holding the longest point first */
+        std::sort(launches.begin(), launches.end(),
+                  [](const Launch& a, const Launch& b) { return a.longest > b.longest; });
+        constexpr int kThreads = 512;
+        cudaEvent_t ready = nullptr;
+        BCU(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+        BCU(cudaEventRecord(ready, st));
+        std::vector<cudaStream_t> side(launches.size(), nullptr);
+        std::vector<cudaEvent_t> done(launches.size(), nullptr);
+        int r = 0;
+        for (size_t c = 0; c < launches.size() && !r; ++c) {
+            const Launch& L = launches[c];
+            bte::ResArgs<T> ra;
+            ra.inst = ba.inst;
+            ra.order = reinterpret_cast<const int*>(mem + map_off) + L.begin;
+            ra.count = L.count;
+            ra.queue = reinterpret_cast<unsigned*>(mem + base_off) + c;
+            ra.C = L.C;
+            ra.red_off = L.arrays;
+            int clusters = 0;
+            r = bte::resident_max_clusters<T>(L.C, L.smem, kThreads, &clusters);
+            if (r || clusters < 1) {
+                rc = fail(BTE_ECUDA, "on-chip kernel: no cluster of %d CTAs with %zu bytes fits (%s)",
+                          L.C, L.smem, cudaGetErrorString((cudaError_t)r));
+                r = -1;
+                break;
+            }
+            clusters = std::min(clusters, L.count);
+            if (cudaStreamCreateWithFlags(&side[c], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&done[c], cudaEventDisableTiming) != cudaSuccess ||
+                cudaStreamWaitEvent(side[c], ready, 0) != cudaSuccess) {
+                rc = fail(BTE_ECUDA, "on-chip launch: stream setup failed");
+                r = -1;
+                break;
+            }
+            r = bte::launch_resident<T>(ra, clusters, kThreads, L.smem, side[c]);
+            if (r) {
+                rc = fail(BTE_ECUDA, "on-chip kernel launch: %s", cudaGetErrorString((cudaError_t)r));
+                break;
+            }
+            if (cudaEventRecord(done[c], side[c]) != cudaSuccess ||
+                cudaStreamWaitEvent(st, done[c], 0) != cudaSuccess) {
+                rc = fail(BTE_ECUDA, "on-chip launch: join failed");
+                r = -1;
+                break;
+            }
+        }
+        for (size_t c = 0; c < side.size(); ++c) {
+            if (side[c]) {
+                cudaStreamSynchronize(side[c]);
+                cudaStreamDestroy(side[c]);
+            }
+            if (done[c]) cudaEventDestroy(done[c]);
+        }
+        cudaEventDestroy(ready);
+        if (r) {
+            cleanup();
+            return rc;
+        }
+    } else {
     {
         int bps = 0, dev = 0, sms = 0;
         BCU(cudaGetDevice(&dev));
@@ -782,6 +885,7 @@ int run_batch(const bte_params* p, std::vector<BatchPoint>& pts, size_t first, s
             return rc;
         }
     }
+    }  // streamed tier
     /* window averages and status of every instance */
     std::vector<unsigned char> acc_host(tables_end - tables_begin);
     int err = 0;
@@ -871,12 +975,34 @@ int bte_batch_run(const bte_params* p, int32_t n, bte_obs* out, const bte_batch_
     const int max_batch = (opts && opts->max_batch > 0) ? opts->max_batch : 1024;
     const long long max_bytes =
         (opts && opts->max_batch_bytes > 0) ? opts->max_batch_bytes : (4ll << 30);
+    const int mode = opts ? opts->resident : 0;
+    if (mode < 0 || mode > 2) return fail(BTE_EINVAL, "resident must be 0, 1 or 2");
+    const long long budget = (opts && opts->resident_smem > 0) ? opts->resident_smem : 113664;
+    if (budget > 232448) return fail(BTE_EINVAL, "resident_smem above 232,448 bytes");
+    if (opts && opts->reserved) return fail(BTE_EINVAL, "reserved field must be 0");
     for (auto& b : pts) {
         b.ntx = (b.M1 + tile - 1) / tile;
         b.nty = (b.N1 + chunk - 1) / chunk;
+        /* smallest cluster whose CTAs hold the point in `budget` bytes each,
+         * with at least two rows per CTA (rows 0 and 1 in the first CTA) */
+        b.resC = 0;
+        if (mode != 1)
+            for (int C = 1; C <= 16; C *= 2) {
+                if (C > 1 && (b.N1 + C - 1) / C < 2) break;
+                const size_t need = fp64 ? bte::resident_smem_bytes<double>(b.N1 - 1, b.M1 - 1, C, nullptr)
+                                         : bte::resident_smem_bytes<float>(b.N1 - 1, b.M1 - 1, C, nullptr);
+                if ((long long)need <= budget) {
+                    b.resC = C;
+                    break;
+                }
+            }
+        if (mode == 2 && !b.resC)
+            return fail(BTE_EINVAL, "point %d does not fit on chip in %lld bytes per CTA", b.idx, budget);
     }
-    /* longest runs first, so a batch's members need similar step counts */
+    /* by tier (on-chip cluster size, then streamed), longest runs first, so a
+     * streamed batch's members need similar step counts */
     std::sort(pts.begin(), pts.end(), [](const BatchPoint& x, const BatchPoint& y) {
+        if (x.resC != y.resC) return x.resC > y.resC;
         return x.tg.K != y.tg.K ? x.tg.K > y.tg.K : x.idx < y.idx;
     });
     cudaStream_t st = opts && opts->stream ? (cudaStream_t)opts->stream : nullptr;
@@ -897,16 +1023,20 @@ int bte_batch_run(const bte_params* p, int32_t n, bte_obs* out, const bte_batch_
     while (first < pts.size()) {
         size_t last = first;
         long long bytes = 0;
-        while (last < pts.size() && (int)(last - first) < max_batch) {
+        /* on-chip points of every cluster size share a batch */
+        const int resC = pts[first].resC;
+        while (last < pts.size() && (pts[last].resC > 0) == (resC > 0) &&
+               (resC > 0 || (int)(last - first) < max_batch)) {
             const BatchPoint& b = pts[last];
             const long long pitch = (long long)align_up((size_t)(128 / elem + b.ntx * tile + 32 / elem), 32);
-            const long long sb = 8ll * b.N1 * pitch * elem + 2ll * (b.tg.P + 2) * 8 + 4096;
+            const long long sb = (resC > 0 ? 4ll : 8ll) * b.N1 * pitch * elem + 2ll * (b.tg.P + 2) * 8 + 4096;
             if (last > first && bytes + sb > max_bytes) break;
             bytes += sb;
             ++last;
         }
-        const int rc = fp64 ? run_batch<double>(p, pts, first, last, tile, chunk, vec, graph_len, st, cap, out)
-                            : run_batch<float>(p, pts, first, last, tile, chunk, vec, graph_len, st, cap, out);
+        const bool res = resC > 0;
+        const int rc = fp64 ? run_batch<double>(p, pts, first, last, tile, chunk, vec, graph_len, res, st, cap, out)
+                            : run_batch<float>(p, pts, first, last, tile, chunk, vec, graph_len, res, st, cap, out);
         if (rc == BTE_ECUDA || rc == BTE_ENOMEM) {
             worst = rc;
             break;

@@ -95,6 +95,20 @@ struct BatchArgs {
     int tile_m, chunk_n, vec, grid;
 };
 
+/* Arguments of the on-chip batched kernel (bte_resident.cu): clusters of C
+ * CTAs take points order[0..count) from the queue counter; each CTA holds
+ * ceil((N+1)/C) harmonic rows of its point in shared memory; the per-warp
+ * partial sums start at byte red_off, after the largest point's arrays. */
+template <typename T>
+struct ResArgs {
+    const BatchInst<T>* inst;
+    const int* order;
+    int count;
+    unsigned* queue;
+    int C;
+    size_t red_off;
+};
+
 /* One plain application of T (start-up half step), unfused. */
 template <typename T>
 struct ApplyArgs {
@@ -139,6 +153,15 @@ int launch_observe(const T* a_w, const T* b_w, int M, int pitch, double vscale,
                    void* stream);
 int launch_advance_base(long long* base, long long by, void* stream);
 int launch_finalize(const FinalArgs& a, void* stream);
+/* On-chip batched kernel: shared memory a CTA needs for a point of N+1
+ * harmonics and M+1 columns split over C CTAs (*arrays_bytes: the part
+ * before the warp partials), clusters that fit the GPU at once, launch. */
+template <typename T>
+size_t resident_smem_bytes(int N, int M, int C, size_t* arrays_bytes);
+template <typename T>
+int resident_max_clusters(int C, size_t smem, int threads, int* clusters);
+template <typename T>
+int launch_resident(const ResArgs<T>& a, int clusters, int threads, size_t smem, void* stream);
 /* Sets the calling thread's bte_last_error() message; returns code. */
 int report_error(int code, const char* msg);
 template <typename T>

@@ -1,0 +1,420 @@
+/*
+ * bte_resident.cu -- batched solver with the state resident on chip.
+ *
+ * One thread-block cluster (C CTAs, C in 1..16) owns one parameter point at
+ * a time and keeps its four grid arrays (a, b of the whole and fractional
+ * grids, Sec. 3) in the CTAs' shared memory for every step of the run: CTA
+ * r holds harmonic rows [r R, (r+1) R) over all phi_y columns, plus one halo
+ * row above and below.  A time step is the two half-steps of the leap-frog
+ * scheme (Eqs. leap_frog_1, leap_frog_2), each applied in place -- the whole
+ * grid's update reads only the fractional grid and each cell's own value,
+ * and vice versa -- with a cluster barrier after each half-step and the
+ * halo rows then read from the neighbouring CTAs' shared memory.  Per-cell
+ * operations are those of the streaming kernel, in the same order (the
+ * compiler may still contract multiply-adds differently); the per-step sums
+ * of rows 0 and 1 (Eqs. v_dr_generic, norm_in_phi) are added in another
+ * order.
+ *
+ * Clusters take points from a queue (an atomic counter over a list sorted
+ * by cost); there are no spin-waits: the only waits are cluster barriers,
+ * which every CTA of a cluster passes the same number of times (all CTAs
+ * run the same point for the same number of steps).
+ */
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "bte_device.cuh"
+#include "bte_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace bte {
+namespace {
+
+using dev::cn_cell;
+
+template <typename T>
+struct RV {
+    static constexpr int V = 16 / (int)sizeof(T); /* columns per work unit (16 bytes) */
+};
+
+template <typename T>
+__device__ __forceinline__ void ld_vec(const T* p, T (&x)[RV<T>::V]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        x[0] = v.x;
+        x[1] = v.y;
+        x[2] = v.z;
+        x[3] = v.w;
+    } else {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        x[0] = v.x;
+        x[1] = v.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void st_vec(T* p, const T (&x)[RV<T>::V]) {
+    if constexpr (sizeof(T) == 4)
+        *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    else
+        *reinterpret_cast<double2*>(p) = make_double2(x[0], x[1]);
+}
+
+/* central differences x[m+1] - x[m-1] of a group, the outer neighbours
+ * taken from the adjacent lanes' groups where those are the adjacent
+ * columns (l_adj / r_adj), else loaded.  Every lane of the warp must call
+ * it (the shuffles need the full warp). */
+template <typename T>
+__device__ __forceinline__ void diff_sh(const T* p, bool l_adj, bool r_adj, T (&d)[RV<T>::V]) {
+    constexpr int V = RV<T>::V;
+    T own[V];
+    ld_vec<T>(p, own);
+    const T from_l = __shfl_up_sync(0xffffffffu, own[V - 1], 1);
+    const T from_r = __shfl_down_sync(0xffffffffu, own[0], 1);
+    const T left = l_adj ? from_l : p[-1];
+    const T right = r_adj ? from_r : p[V];
+    d[0] = own[1] - left;
+#pragma unroll
+    for (int e = 1; e < V - 1; ++e) d[e] = own[e + 1] - own[e - 1];
+    d[V - 1] = right - own[V - 2];
+}
+
+/* global array a of a point: 0 a_w, 1 b_w, 2 a_f, 3 b_f */
+template <typename T>
+__device__ __forceinline__ T* gsel(const BatchInst<T>& I, int a) {
+    return a == 0 ? I.a_w[0] : a == 1 ? I.b_w[0] : a == 2 ? I.a_f[0] : I.b_f[0];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
+    constexpr int V = RV<T>::V;
+    constexpr int LG = V;              /* local ghost columns before m = 0 */
+    constexpr int GG = Cols<T>::G;     /* global ghost columns before m = 0 */
+    extern __shared__ __align__(16) unsigned char smem[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int C = A.C;
+    double* red = reinterpret_cast<double*>(smem + A.red_off); /* [2][32] warp partials */
+    int* s_next = reinterpret_cast<int*>(red + 64);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = (nthr + 31) >> 5;
+
+    for (;;) {
+        if (rank == 0 && tid == 0) *s_next = (int)atomicAdd(A.queue, 1u);
+        cl.sync();
+        const int qi = *cl.map_shared_rank(s_next, 0);
+        cl.sync(); /* every CTA has read the index before rank 0 may replace it */
+        if (qi >= A.count) break;
+        const BatchInst<T>& I = A.inst[A.order[qi]];
+        const int N = I.N, M = I.M, N1 = N + 1, gp = I.pitch, PP = I.P;
+        const int rows_per = (N1 + C - 1) / C;
+        const int r0 = min(N1, rank * rows_per), r1 = min(N1, r0 + rows_per), R = r1 - r0;
+        const int ncg = (M + 1 + V - 1) / V;
+        const long long K = I.K, Kw = I.Kw;
+        const T h = I.h, hh = I.hh, nu = I.nu, xi = I.xi, cc = I.c;
+        /* shared-memory layout of this point: 4 arrays of rows_per + 2 rows
+         * (halo, own rows, halo) with row stride P = ghost + columns + ghost */
+        const int P = LG + ncg * V + V;
+        const size_t arr = (size_t)(rows_per + 2) * P;
+        T* sAw = reinterpret_cast<T*>(smem);
+        T* sBw = sAw + arr;
+        T* sAf = sBw + arr;
+        T* sBf = sAf + arr;
+        T* sG = sBf + arr; /* [P] column factor of a0 */
+        T* sBp = sG + P;   /* [P] B phi_m */
+        T* sR = sBp + P;   /* [rows_per + 2] row factor of a0, rows r0-1 .. r0+rows_per */
+
+        /* ---- load: zero everything, then rows r0-1 .. r1 that exist ---- */
+        for (size_t q = tid; q < 4 * arr + 2 * (size_t)P + rows_per + 2; q += nthr) sAw[q] = (T)0;
+        __syncthreads();
+        {
+            const int rows = R + 2;
+            for (int q = tid; q < 4 * rows * ncg; q += nthr) {
+                const int a = q / (rows * ncg);
+                const int rem = q - a * rows * ncg;
+                const int li = rem / ncg, g = rem - li * ncg;
+                const int n = r0 - 1 + li;
+                if (n < 0 || n > N) continue;
+                T v[V];
+                ld_vec<T>(gsel(I, a) + (size_t)n * gp + GG + g * V, v);
+                st_vec<T>(sAw + a * arr + (size_t)li * P + LG + g * V, v);
+            }
+            for (int q = tid; q < ncg * V; q += nthr) {
+                sG[LG + q] = I.col_g[GG + q];
+                sBp[LG + q] = I.col_bphi[GG + q];
+            }
+            for (int q = tid; q < R + 2; q += nthr) {
+                const int n = r0 - 1 + q;
+                sR[q] = (n >= 0 && n <= N) ? I.row_a0[n] : (T)0;
+            }
+        }
+        __syncthreads();
+
+        /* window accumulators (thread 0 of rank 0) */
+        double acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0, acc4 = 0, acc5 = 0;
+        /* the four arrays of a CTA are contiguous, arr elements apart */
+        const T* nbr_up = rank > 0 ? cl.map_shared_rank(sAw, rank - 1) : sAw;
+        const T* nbr_dn = rank < C - 1 ? cl.map_shared_rank(sAw, rank + 1) : sAw;
+        const bool have_up = r0 >= 1 && R > 0, have_dn = r1 <= N && R > 0;
+        /* halo copy of arrays a0, a0+1 (0/1: whole grid, 2/3: fractional):
+         * row r0-1 is the last row of rank-1 (its local row rows_per-1),
+         * row r1 the first row of rank+1 (its local row 0) */
+        auto halo = [&](int a0) {
+            for (int q = tid; q < 4 * ncg; q += nthr) {
+                const int which = q / ncg, g = q - which * ncg;
+                const int a = a0 + (which & 1);
+                const bool up = which < 2;
+                if (up ? !have_up : !have_dn) continue;
+                const T* src = up ? nbr_up + a * arr + (size_t)rows_per * P
+                                  : nbr_dn + a * arr + (size_t)1 * P;
+                T* dst = sAw + a * arr + (up ? (size_t)0 : (size_t)(R + 1) * P);
+                T v[V];
+                ld_vec<T>(src + LG + g * V, v);
+                st_vec<T>(dst + LG + g * V, v);
+            }
+        };
+
+        /* thread -> (column group, row phase), fixed for the point: a pass
+         * covers cpp consecutive column groups, rsplit rows at a time; every
+         * thread runs the same number of iterations (warp shuffles below) */
+        const int cpp = min(ncg, nthr);
+        const int rsplit = nthr / cpp;
+        const int gl = tid % cpp, rp = tid / cpp;
+        const bool t_on = rp < rsplit;
+        const int npass = (ncg + cpp - 1) / cpp;
+        const int nrow = (R + rsplit - 1) / rsplit;
+        for (long long k = 0; k < K; ++k) {
+            const int kk = PP > 0 ? (int)(k % PP) : 0;
+            const T Ews = (T)I.e_whole[kk], Ewe = (T)I.e_whole[kk + 1];
+            const T Efs = (T)I.e_frac[kk], Efe = (T)I.e_frac[kk + 1];
+            double part_n = 0.0, part_v = 0.0;
+            /* ---- whole grid: z_w^{k+1} = T(z_w^k; S(z_f^{k+1/2})) ---- */
+            for (int pass = 0; pass < npass; ++pass) {
+                const int g = pass * cpp + gl;
+                const bool g_on = t_on && g < ncg;
+                const int m0 = (g_on ? g : 0) * V;
+                const bool l_adj = lane > 0 && gl > 0;
+                const bool r_adj = lane < 31 && gl + 1 < cpp && g + 1 < ncg;
+                T gc[V], ws[V], we[V];
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    const T bp = sBp[LG + m0 + e];
+                    gc[e] = sG[LG + m0 + e];
+                    ws[e] = (Ews + bp) * hh;
+                    we[e] = (Ewe + bp) * hh;
+                }
+                for (int ii = 0; ii < nrow; ++ii) {
+                    const int i = rp + ii * rsplit;
+                    const bool on = g_on && i < R;
+                    const int il = on ? i : 0;
+                    const int n = r0 + il;
+                    const size_t o = (size_t)(il + 1) * P + LG + m0;
+                    T oa[V], ob[V], dfa_p1[V], dfa_m1[V], dfb_p1[V], dfb_m1[V];
+                    ld_vec<T>(sAw + o, oa);
+                    ld_vec<T>(sBw + o, ob);
+                    diff_sh<T>(sAf + o + P, l_adj, r_adj, dfa_p1);
+                    diff_sh<T>(sAf + o - P, l_adj, r_adj, dfa_m1);
+                    diff_sh<T>(sBf + o + P, l_adj, r_adj, dfb_p1);
+                    diff_sh<T>(sBf + o - P, l_adj, r_adj, dfb_m1);
+                    if (!on) continue;
+                    const T nf = (T)n;
+                    const T chi = (n == 1) ? (T)2 : (T)1;
+                    const T ha0 = h * sR[il + 1];
+                    T wa[V], wb[V];
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        T an, bn;
+                        cn_cell<T>(oa[e], ob[e], cc * (dfb_p1[e] - dfb_m1[e]),
+                                   cc * (chi * dfa_m1[e] - dfa_p1[e]), ha0 * gc[e], nf * ws[e],
+                                   nf * we[e], nu, xi, h, an, bn);
+                        const bool ok = m0 + e <= M;
+                        wa[e] = ok ? an : (T)0;
+                        wb[e] = (ok && n > 0) ? bn : (T)0;
+                    }
+                    st_vec<T>(sAw + o, wa);
+                    st_vec<T>(sBw + o, wb);
+                    if (n == 0)
+#pragma unroll
+                        for (int e = 0; e < V; ++e) part_n += (double)wa[e];
+                    if (n == 1)
+#pragma unroll
+                        for (int e = 0; e < V; ++e) part_v += (double)wb[e];
+                }
+            }
+            if (rank == 0) {
+                part_n = warp_sum(part_n);
+                part_v = warp_sum(part_v);
+                if (lane == 0) {
+                    red[warp] = part_n;
+                    red[32 + warp] = part_v;
+                }
+            }
+            cl.sync();
+            halo(0);
+            __syncthreads();
+            if (rank == 0 && tid == 0) {
+                double sn = 0, sv = 0;
+                for (int w = 0; w < nwarp; ++w) {
+                    sn += red[w];
+                    sv += red[32 + w];
+                }
+                const double vv = I.vscale * sv, nn = I.nscale * sn;
+                const long long k1 = k + 1;
+                if (k1 > K - Kw) {
+                    const double ang = PP > 0 ? 6.283185307179586476925286766559 *
+                                                    (double)(k1 % PP) / (double)PP
+                                              : I.omega * (double)k1 * I.dt_eff;
+                    acc0 += vv * cos(ang);
+                    acc1 += vv;
+                }
+                acc2 = fmax(acc2, fabs(nn - 1.0));
+                if (!isfinite(vv) || !isfinite(nn)) acc3 = 1.0;
+                acc4 = vv;
+                acc5 = nn;
+            }
+            /* ---- fractional grid: z_f^{k+3/2} = T(z_f^{k+1/2}; S(z_w^{k+1})) ---- */
+            for (int pass = 0; pass < npass; ++pass) {
+                const int g = pass * cpp + gl;
+                const bool g_on = t_on && g < ncg;
+                const int m0 = (g_on ? g : 0) * V;
+                const bool l_adj = lane > 0 && gl > 0;
+                const bool r_adj = lane < 31 && gl + 1 < cpp && g + 1 < ncg;
+                T gc[V], fs[V], fe[V];
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    const T bp = sBp[LG + m0 + e];
+                    gc[e] = sG[LG + m0 + e];
+                    fs[e] = (Efs + bp) * hh;
+                    fe[e] = (Efe + bp) * hh;
+                }
+                for (int ii = 0; ii < nrow; ++ii) {
+                    const int i = rp + ii * rsplit;
+                    const bool on = g_on && i < R;
+                    const int il = on ? i : 0;
+                    const int n = r0 + il;
+                    const size_t o = (size_t)(il + 1) * P + LG + m0;
+                    T fa[V], fb[V], dwa_0[V], dwa_m2[V], dwb_0[V], dwb_m2[V];
+                    ld_vec<T>(sAf + o, fa);
+                    ld_vec<T>(sBf + o, fb);
+                    diff_sh<T>(sAw + o + P, l_adj, r_adj, dwa_0);
+                    diff_sh<T>(sAw + o - P, l_adj, r_adj, dwa_m2);
+                    diff_sh<T>(sBw + o + P, l_adj, r_adj, dwb_0);
+                    diff_sh<T>(sBw + o - P, l_adj, r_adj, dwb_m2);
+                    if (!on) continue;
+                    const T nf = (T)n;
+                    const T chi = (n == 1) ? (T)2 : (T)1;
+                    const T ha0 = h * sR[il + 1];
+                    T na[V], nb[V];
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        T an, bn;
+                        cn_cell<T>(fa[e], fb[e], cc * (dwb_0[e] - dwb_m2[e]),
+                                   cc * (chi * dwa_m2[e] - dwa_0[e]), ha0 * gc[e], nf * fs[e],
+                                   nf * fe[e], nu, xi, h, an, bn);
+                        if (n == 0) bn = (T)0;
+                        const bool ok = m0 + e <= M;
+                        na[e] = ok ? an : (T)0;
+                        nb[e] = ok ? bn : (T)0;
+                    }
+                    st_vec<T>(sAf + o, na);
+                    st_vec<T>(sBf + o, nb);
+                }
+            }
+            cl.sync();
+            halo(2);
+            __syncthreads();
+        }
+
+        /* ---- results: window sums, final state ---- */
+        if (rank == 0 && tid == 0) {
+            I.acc[0] = acc0;
+            I.acc[1] = acc1;
+            I.acc[2] = acc2;
+            I.acc[3] = acc3;
+            I.acc[4] = acc4;
+            I.acc[5] = acc5;
+        }
+        for (int q = tid; q < 4 * R * ncg; q += nthr) {
+            const int a = q / (R * ncg);
+            const int rem = q - a * R * ncg;
+            const int i = rem / ncg, g = rem - i * ncg;
+            T v[V];
+            ld_vec<T>(sAw + a * arr + (size_t)(i + 1) * P + LG + g * V, v);
+            st_vec<T>(gsel(I, a) + (size_t)(r0 + i) * gp + GG + g * V, v);
+        }
+        /* the next point's load overwrites shared memory that neighbours
+         * may still read in their last halo copy: wait for the cluster */
+        cl.sync();
+    }
+}
+
+}  // namespace
+
+template <typename T>
+size_t resident_smem_bytes(int N, int M, int C, size_t* arrays_bytes) {
+    constexpr int V = RV<T>::V;
+    const int rows_per = (N + 1 + C - 1) / C;
+    const int ncg = (M + 1 + V - 1) / V;
+    const size_t P = (size_t)(V + ncg * V + V);
+    const size_t arr = (size_t)(rows_per + 2) * P;
+    size_t b = (4 * arr + 2 * P + rows_per + 2) * sizeof(T);
+    b = (b + 15) / 16 * 16;
+    if (arrays_bytes) *arrays_bytes = b;
+    return b + 64 * sizeof(double) + 16;
+}
+
+template <typename T>
+int resident_max_clusters(int C, size_t smem, int threads, int* clusters) {
+    cudaError_t e = cudaFuncSetAttribute(resident_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && C > 8)
+        e = cudaFuncSetAttribute(resident_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return (int)e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaOccupancyMaxActiveClusters(clusters, resident_kernel<T>, &cfg);
+    return (int)e;
+}
+
+template <typename T>
+int launch_resident(const ResArgs<T>& a, int clusters, int threads, size_t smem, void* stream) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(clusters * a.C, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = a.C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, resident_kernel<T>, a);
+    return e == cudaSuccess ? 0 : (int)e;
+}
+
+template size_t resident_smem_bytes<float>(int, int, int, size_t*);
+template size_t resident_smem_bytes<double>(int, int, int, size_t*);
+template int resident_max_clusters<float>(int, size_t, int, int*);
+template int resident_max_clusters<double>(int, size_t, int, int*);
+template int launch_resident<float>(const ResArgs<float>&, int, int, size_t, void*);
+template int launch_resident<double>(const ResArgs<double>&, int, int, size_t, void*);
+
+}  // namespace bte

@@ -232,7 +232,8 @@ class Surrogate:
         solved = np.zeros(n, dtype=np.uint8)
         status = np.zeros(n, dtype=np.int32)
         o = bte.bte_batch_opts()
-        for k in ("tile_m", "chunk_n", "vec", "graph_steps", "max_batch", "max_batch_bytes"):
+        for k in ("tile_m", "chunk_n", "vec", "graph_steps", "max_batch", "max_batch_bytes",
+                  "resident", "resident_smem"):
             setattr(o, k, int(batch_opts.get(k, 0)))
         o.reserved = 0
         o.stream = None

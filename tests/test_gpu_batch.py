@@ -62,7 +62,7 @@ def _same_obs(o, r, exact_window=False):
 def test_batch_equals_single_instance(prec, vec):
     pts = _mixed_points(prec)
     tile, chunk = 32 * vec, 8
-    res = bte.batch_run(pts, tile_m=tile, chunk_n=chunk, vec=vec)
+    res = bte.batch_run(pts, tile_m=tile, chunk_n=chunk, vec=vec, resident=1)
     for p, o in zip(pts, res):
         r = bte.solve(p, tile_m=tile, chunk_n=chunk, vec=vec)
         _same_obs(o, r)
@@ -107,8 +107,8 @@ def test_batch_split_into_several_batches_is_bitwise():
 
 def test_batch_graph_and_direct_launches_agree():
     pts = _mixed_points(W.FP64, seed=19, n=4)
-    g = bte.batch_run(pts, graph_steps=256)
-    d = bte.batch_run(pts, graph_steps=1)
+    g = bte.batch_run(pts, graph_steps=256, resident=1)
+    d = bte.batch_run(pts, graph_steps=1, resident=1)
     for a, b in zip(g, d):
         _same_obs(a, b, exact_window=True)
 
@@ -119,9 +119,9 @@ def test_batch_reports_unstable_point_and_keeps_the_rest():
                    phiy_min=-5, phiy_max=5, dt=0.05, t_max=20.0, avg_window=1.0)
     pts = good[:1] + [bad] + good[1:]
     with pytest.raises(bte.BteError) as e:
-        bte.batch_run(pts)
+        bte.batch_run(pts, resident=1)
     assert e.value.code == bte.EUNSTABLE
-    res = bte.batch_run(pts, check=False)
+    res = bte.batch_run(pts, check=False, resident=1)
     assert res[1].status == bte.EUNSTABLE
     for p, o in zip(pts[:1] + pts[2:], res[:1] + res[2:]):
         r = bte.solve(p, tile_m=128, chunk_n=16)

@@ -1,0 +1,129 @@
+"""On-chip tier of bte_batch_run: each point held in the shared memory of a
+thread-block cluster for its whole run.
+
+The per-cell operations are the streamed tier's; the compiler may contract
+a multiply and an add into one FMA differently in the two kernels, and the
+per-step phi_y sums are added in another order.  So in FP64 every
+observable agrees with the streamed tier to 1e-12 relative; in FP32 to the
+FP32 rounding level (2e-6 absolute on drift velocity and absorption, 1e-7
+on the norm).  Against the FP64 oracle the bar is 1e-10 relative (FP64) and
+1e-5 absolute (FP32)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_6047_gb300 import bte
+from paper_1401_6047_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _points(prec, seed, n=6, n_lo=6, n_hi=40, m_lo=40, m_hi=300):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        L = float(rng.uniform(4.0, 9.0))
+        out.append(W.Params(E_dc=float(rng.uniform(0.0, 4.0)), E_omega=float(rng.uniform(0.05, 1.0)),
+                            omega=float(rng.uniform(1.0, 4.0)), B=float(rng.uniform(0.0, 3.0)),
+                            mu=float(rng.uniform(0.5, 4.0)), n_max=int(rng.integers(n_lo, n_hi)),
+                            m_points=int(rng.integers(m_lo, m_hi)), phiy_min=-L, phiy_max=L,
+                            dt=float(rng.choice([2e-3, 4e-3])), periods=float(rng.choice([1.5, 2.0])),
+                            avg_window=1.0, precision=prec))
+    return out
+
+
+def _close(a, b, rtol=1e-12, atol=1e-15):
+    if math.isnan(b):
+        return math.isnan(a)
+    return abs(a - b) <= rtol * abs(b) + atol
+
+
+def _agree(o, r, fp32=False):
+    assert o.steps_total == r.steps_total and o.window_steps == r.window_steps
+    assert o.status == r.status
+    for k in ("v_dr", "norm", "v_dc_avg", "absorption", "norm_max_abs_err"):
+        if fp32:
+            tol = 1e-7 if k in ("norm", "norm_max_abs_err") else 2e-6
+            ok = _close(getattr(o, k), getattr(r, k), rtol=0.0, atol=tol)
+        else:
+            ok = _close(getattr(o, k), getattr(r, k))
+        assert ok, (k, getattr(o, k), getattr(r, k))
+
+
+# shared memory per CTA (FP32 figures, doubled for FP64) that spreads the
+# points below over clusters of 1 to 16 CTAs; 34,000 still holds the largest
+# (60 x 299) in 16 CTAs
+@pytest.mark.parametrize("smem", [0, 60000, 45000, 34000])
+@pytest.mark.parametrize("prec", [W.FP64, W.FP32_MIXED])
+def test_on_chip_equals_streamed(prec, smem):
+    pts = _points(prec, seed=31, n=7, n_lo=32, n_hi=60)
+    if smem and prec == W.FP64:
+        smem *= 2
+    on = bte.batch_run(pts, resident=2, resident_smem=smem)
+    st = bte.batch_run(pts, resident=1)
+    for o, r in zip(on, st):
+        _agree(o, r, prec == W.FP32_MIXED)
+
+
+def test_on_chip_fp64_matches_oracle():
+    pts = _points(W.FP64, seed=37)
+    res = bte.batch_run(pts, resident=2)
+    for p, o in zip(pts, res):
+        ref = oracle.solve(p)
+        assert abs(o.absorption - ref.A) <= 1e-10 * abs(ref.A) + 1e-15
+        assert abs(o.v_dc_avg - ref.v_dc) <= 1e-10 * abs(ref.v_dc) + 1e-15
+        assert abs(o.norm_max_abs_err - ref.norm_err) <= 1e-13
+
+
+def test_on_chip_fp32_within_1e5_of_oracle():
+    pts = _points(W.FP32_MIXED, seed=41)
+    res = bte.batch_run(pts, resident=2, resident_smem=30000)
+    for p, o in zip(pts, res):
+        ref = oracle.solve(p)
+        assert abs(o.absorption - ref.A) <= 1e-5
+        assert abs(o.v_dc_avg - ref.v_dc) <= 1e-5
+
+
+def test_mixed_tiers_in_one_call():
+    """Small points on chip, a large one streamed, results in input order."""
+    small = _points(W.FP32_MIXED, seed=43, n=4)
+    big = W.Params(E_dc=2.0, E_omega=0.5, omega=2.0, B=2.0, mu=2.0, n_max=120, m_points=3001,
+                   phiy_min=-20, phiy_max=20, dt=4e-3, periods=1.0, avg_window=1.0,
+                   precision=W.FP32_MIXED)
+    pts = small[:2] + [big] + small[2:]
+    auto = bte.batch_run(pts)
+    st = bte.batch_run(pts, resident=1)
+    for o, r in zip(auto, st):
+        _agree(o, r, fp32=True)
+    with pytest.raises(bte.BteError) as e:
+        bte.batch_run([big], resident=2, resident_smem=20000)
+    assert e.value.code == bte.EINVAL
+
+
+def test_on_chip_unstable_point_reported():
+    bad = W.Params(E_dc=1.0, E_omega=0.0, omega=0.0, B=40.0, mu=1.0, n_max=12, m_points=101,
+                   phiy_min=-5, phiy_max=5, dt=0.05, t_max=20.0, avg_window=1.0)
+    good = _points(W.FP64, seed=47, n=2)
+    res = bte.batch_run([good[0], bad, good[1]], resident=2, check=False)
+    assert res[1].status == bte.EUNSTABLE
+    assert res[0].status == bte.OK and res[2].status == bte.OK
+
+
+def test_on_chip_zero_omega_point():
+    p = W.Params(E_dc=1.7, E_omega=0.0, omega=0.0, B=1.5, mu=2.0, n_max=20, m_points=161,
+                 phiy_min=-8, phiy_max=8, dt=5e-3, t_max=6.0, avg_window=1.0)
+    o = bte.batch_run([p], resident=2)[0]
+    ref = oracle.solve(p)
+    assert math.isnan(o.absorption)
+    assert abs(o.v_dc_avg - ref.v_dc) <= 1e-10 * abs(ref.v_dc)
+
+
+def test_sweep_sample_on_chip_matches_streamed():
+    """Grid sizes of the 4096-point sweep (shortened runs)."""
+    pts = W.sweep_points(n=4096, periods=0.3, avg_window=0.1)[::256]
+    on = bte.batch_run(pts, resident=2, resident_smem=232448)
+    st = bte.batch_run(pts, resident=1)
+    for o, r in zip(on, st):
+        _agree(o, r, fp32=True)
