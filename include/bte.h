@@ -218,7 +218,7 @@ typedef struct bte_batch_opts {
     int64_t max_batch_bytes; /* device bytes one batch may hold (0: 4 GiB)            */
     void* stream;            /* cudaStream_t to queue on (NULL: a private stream)     */
     int32_t resident_smem;   /* shared memory per CTA for on-chip points, bytes
-                                (0: 113,664, two CTAs per SM; at most 232,448)       */
+                                (0: 232,448, the most a CTA may have)                */
     int32_t reserved;        /* must be 0                                             */
 } bte_batch_opts;
 
@@ -246,6 +246,12 @@ typedef struct bte_batch_opts {
  * not run).  Blocks until done; allocates and frees its device memory. */
 BTE_API int bte_batch_run(const bte_params* p, int32_t n, bte_obs* out,
                           const bte_batch_opts* opts);
+
+/* The tier bte_batch_run would give each point (same validation, no GPU
+ * work): tier[i] = CTAs per cluster of the on-chip tier (1..16) or 0 when
+ * p[i] is streamed.  HOST arrays; BTE_EINVAL as bte_batch_run. */
+BTE_API int bte_batch_plan(const bte_params* p, int32_t n, const bte_batch_opts* opts,
+                           int32_t* tier);
 
 /* Library version string. */
 BTE_API const char* bte_version(void);

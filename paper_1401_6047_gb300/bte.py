@@ -103,6 +103,8 @@ def lib() -> ctypes.CDLL:
             "bte_launch_shape": ([P, T] + [ctypes.POINTER(ctypes.c_int32)] * 5, ctypes.c_int),
             "bte_batch_run": ([P, ctypes.c_int32, ctypes.POINTER(bte_obs),
                                ctypes.POINTER(bte_batch_opts)], ctypes.c_int),
+            "bte_batch_plan": ([P, ctypes.c_int32, ctypes.POINTER(bte_batch_opts),
+                                ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -292,6 +294,29 @@ def _obs(o: bte_obs) -> Observables:
                        o.window_steps, o.status)
 
 
+def _batch_opts(tile_m=0, chunk_n=0, vec=0, graph_steps=0, max_batch=0, max_batch_bytes=0,
+                stream=0, resident=0, resident_smem=0):
+    o = bte_batch_opts()
+    o.tile_m, o.chunk_n, o.vec, o.graph_steps = int(tile_m), int(chunk_n), int(vec), int(graph_steps)
+    o.max_batch, o.resident, o.max_batch_bytes = int(max_batch), int(resident), int(max_batch_bytes)
+    o.resident_smem, o.reserved = int(resident_smem), 0
+    o.stream = ctypes.c_void_p(stream or None)
+    return o
+
+
+def batch_plan(points, **opts) -> np.ndarray:
+    """Tier of every point under ``batch_run`` with the same options
+    (``bte_batch_plan``): CTAs per cluster on chip, 0 when streamed."""
+    pts = list(points)
+    n = len(pts)
+    arr = (bte_params * max(n, 1))(*[to_params(q) for q in pts])
+    tier = np.zeros(max(n, 1), dtype=np.int32)
+    o = _batch_opts(**opts)
+    _check(lib().bte_batch_plan(arr, n, ctypes.byref(o),
+                                tier.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return tier[:n]
+
+
 def batch_run(points, tile_m: int = 0, chunk_n: int = 0, vec: int = 0, graph_steps: int = 0,
               max_batch: int = 0, max_batch_bytes: int = 0, stream: int = 0,
               resident: int = 0, resident_smem: int = 0,
@@ -304,11 +329,8 @@ def batch_run(points, tile_m: int = 0, chunk_n: int = 0, vec: int = 0, graph_ste
     n = len(pts)
     arr = (bte_params * max(n, 1))(*[to_params(q) for q in pts])
     out = (bte_obs * max(n, 1))()
-    o = bte_batch_opts()
-    o.tile_m, o.chunk_n, o.vec, o.graph_steps = int(tile_m), int(chunk_n), int(vec), int(graph_steps)
-    o.max_batch, o.resident, o.max_batch_bytes = int(max_batch), int(resident), int(max_batch_bytes)
-    o.resident_smem, o.reserved = int(resident_smem), 0
-    o.stream = ctypes.c_void_p(stream or None)
+    o = _batch_opts(tile_m, chunk_n, vec, graph_steps, max_batch, max_batch_bytes, stream, resident,
+                    resident_smem)
     rc = lib().bte_batch_run(arr, n, out, ctypes.byref(o))
     if check:
         _check(rc)

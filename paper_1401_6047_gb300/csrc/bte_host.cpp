@@ -925,25 +925,18 @@ int run_batch(const bte_params* p, std::vector<BatchPoint>& pts, size_t first, s
     return worst;
 }
 
-}  // namespace
+struct BatchCfg {
+    bool fp64;
+    int vec, tile, chunk, graph_len, max_batch;
+    long long max_bytes;
+};
 
-namespace bte {
-/* Sets the thread's last-error message for other translation units. */
-int report_error(int code, const char* msg) {
-    g_err = msg ? msg : "";
-    return code;
-}
-}  // namespace bte
-
-extern "C" {
-
-const char* bte_last_error(void) { return g_err.c_str(); }
-
-int bte_batch_run(const bte_params* p, int32_t n, bte_obs* out, const bte_batch_opts* opts) {
-    if (!p || !out || n < 0) return fail(BTE_EINVAL, "bte_batch_run: bad argument");
-    if (n == 0) return BTE_OK;
+/* Validates the points and options of a batched run and assigns each point
+ * its tier (BatchPoint::resC: on-chip cluster size, 0 for streamed). */
+int batch_prepare(const bte_params* p, int32_t n, const bte_batch_opts* opts,
+                  std::vector<BatchPoint>& pts, BatchCfg& cfg) {
     const int prec = p[0].precision;
-    std::vector<BatchPoint> pts(n);
+    pts.assign(n, BatchPoint{});
     for (int i = 0; i < n; ++i) {
         int rc = validate(&p[i]);
         if (rc) return fail(rc, "point %d: %s", i, g_err.c_str());
@@ -977,7 +970,7 @@ int bte_batch_run(const bte_params* p, int32_t n, bte_obs* out, const bte_batch_
         (opts && opts->max_batch_bytes > 0) ? opts->max_batch_bytes : (4ll << 30);
     const int mode = opts ? opts->resident : 0;
     if (mode < 0 || mode > 2) return fail(BTE_EINVAL, "resident must be 0, 1 or 2");
-    const long long budget = (opts && opts->resident_smem > 0) ? opts->resident_smem : 113664;
+    const long long budget = (opts && opts->resident_smem > 0) ? opts->resident_smem : 232448;
     if (budget > 232448) return fail(BTE_EINVAL, "resident_smem above 232,448 bytes");
     if (opts && opts->reserved) return fail(BTE_EINVAL, "reserved field must be 0");
     for (auto& b : pts) {
@@ -999,6 +992,43 @@ int bte_batch_run(const bte_params* p, int32_t n, bte_obs* out, const bte_batch_
         if (mode == 2 && !b.resC)
             return fail(BTE_EINVAL, "point %d does not fit on chip in %lld bytes per CTA", b.idx, budget);
     }
+    cfg.fp64 = fp64;
+    cfg.vec = vec;
+    cfg.tile = tile;
+    cfg.chunk = chunk;
+    cfg.graph_len = graph_len;
+    cfg.max_batch = max_batch;
+    cfg.max_bytes = max_bytes;
+    return BTE_OK;
+}
+
+}  // namespace
+
+namespace bte {
+/* Sets the thread's last-error message for other translation units. */
+int report_error(int code, const char* msg) {
+    g_err = msg ? msg : "";
+    return code;
+}
+}  // namespace bte
+
+extern "C" {
+
+const char* bte_last_error(void) { return g_err.c_str(); }
+
+int bte_batch_run(const bte_params* p, int32_t n, bte_obs* out, const bte_batch_opts* opts) {
+    if (!p || !out || n < 0) return fail(BTE_EINVAL, "bte_batch_run: bad argument");
+    if (n == 0) return BTE_OK;
+    std::vector<BatchPoint> pts;
+    BatchCfg cfg;
+    {
+        const int rc = batch_prepare(p, n, opts, pts, cfg);
+        if (rc) return rc;
+    }
+    const bool fp64 = cfg.fp64;
+    const int vec = cfg.vec, tile = cfg.tile, chunk = cfg.chunk, graph_len = cfg.graph_len;
+    const int max_batch = cfg.max_batch;
+    const long long max_bytes = cfg.max_bytes;
     /* by tier (on-chip cluster size, then streamed), longest runs first, so a
      * streamed batch's members need similar step counts */
     std::sort(pts.begin(), pts.end(), [](const BatchPoint& x, const BatchPoint& y) {
@@ -1048,6 +1078,17 @@ int bte_batch_run(const bte_params* p, int32_t n, bte_obs* out, const bte_batch_
     if (own) cudaStreamDestroy(st);
     if (worst != BTE_OK && g_err.empty()) fail(worst, "at least one point failed");
     return worst;
+}
+
+int bte_batch_plan(const bte_params* p, int32_t n, const bte_batch_opts* opts, int32_t* tier) {
+    if (!p || !tier || n < 0) return fail(BTE_EINVAL, "bte_batch_plan: bad argument");
+    if (n == 0) return BTE_OK;
+    std::vector<BatchPoint> pts;
+    BatchCfg cfg;
+    const int rc = batch_prepare(p, n, opts, pts, cfg);
+    if (rc) return rc;
+    for (const BatchPoint& b : pts) tier[b.idx] = b.resC;
+    return BTE_OK;
 }
 
 const char* bte_version(void) { return "bte-gb300 0.1 (sm_103a)"; }

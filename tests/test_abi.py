@@ -107,3 +107,20 @@ def test_batch_run_rejects_bad_input_on_host(case):
 
 def test_batch_run_of_nothing_is_ok():
     assert bte.batch_run([]) == []
+
+
+def test_batch_plan_assigns_tiers_on_host():
+    """bte_batch_plan: on-chip cluster sizes grow as the per-CTA budget
+    shrinks, streamed (0) when told so or when nothing fits."""
+    pts = [W.Params(n_max=40, m_points=401, precision=W.FP32_MIXED),
+           W.Params(n_max=200, m_points=2001, precision=W.FP32_MIXED),
+           W.Params(n_max=400, m_points=4001, precision=W.FP32_MIXED)]
+    big = bte.batch_plan(pts)
+    small = bte.batch_plan(pts, resident_smem=40000)
+    assert list(bte.batch_plan(pts, resident=1)) == [0, 0, 0]
+    assert big[0] >= 1 and big[2] == 0            # 401 x 4001 never fits on chip
+    assert small[0] >= big[0]
+    assert all(t in (0, 1, 2, 4, 8, 16) for t in list(big) + list(small))
+    with pytest.raises(bte.BteError) as e:
+        bte.batch_plan(pts, resident=2)
+    assert e.value.code == bte.EINVAL
