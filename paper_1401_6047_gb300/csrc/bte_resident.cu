@@ -80,6 +80,68 @@ __device__ __forceinline__ void diff_sh(const T* p, bool l_adj, bool r_adj, T (&
     d[V - 1] = right - own[V - 2];
 }
 
+/* central differences of a group with the outer neighbours loaded (any
+ * address space: used where a row may be a neighbour CTA's) */
+template <typename T>
+__device__ __forceinline__ void diff_ld(const T* p, T (&d)[RV<T>::V]) {
+    constexpr int V = RV<T>::V;
+    T own[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) own[e] = p[e];
+    const T left = p[-1], right = p[V];
+    d[0] = own[1] - left;
+#pragma unroll
+    for (int e = 1; e < V - 1; ++e) d[e] = own[e + 1] - own[e - 1];
+    d[V - 1] = right - own[V - 2];
+}
+
+/* One half-step (Sec. 3, Eqs. a_t_plus_1, b_t_plus_1, in increment form) on
+ * the V cells of a group at harmonic n, in place: oA, oB the own grid's a, b;
+ * da_u, da_d, db_u, db_d the phi_y differences of the other grid's a and b
+ * in rows n-1 (u) and n+1 (d); t0, t1 the drive/field factors
+ * (E + B phi_m) dt/4 at the start and end of the half-step.  Same
+ * expressions as the streaming kernel.  With `whole`, adds row 0's a and
+ * row 1's b to the norm / drift sums. */
+template <typename T>
+__device__ __forceinline__ void cell_group(T* oA, T* oB, const T (&da_u)[RV<T>::V],
+                                           const T (&da_d)[RV<T>::V], const T (&db_u)[RV<T>::V],
+                                           const T (&db_d)[RV<T>::V], int n, int m0, int M, T ha0,
+                                           const T (&gc)[RV<T>::V], const T (&t0)[RV<T>::V],
+                                           const T (&t1)[RV<T>::V], T nu, T xi, T h, T cc,
+                                           bool whole, double& pn, double& pv) {
+    constexpr int V = RV<T>::V;
+    T oa[V], ob[V], na[V], nb[V];
+    ld_vec<T>(oA, oa);
+    ld_vec<T>(oB, ob);
+    const T nf = (T)n;
+    const T chi = (n == 1) ? (T)2 : (T)1;
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        T an, bn;
+        cn_cell<T>(oa[e], ob[e], cc * (db_d[e] - db_u[e]), cc * (chi * da_u[e] - da_d[e]),
+                   ha0 * gc[e], nf * t0[e], nf * t1[e], nu, xi, h, an, bn);
+        const bool ok = m0 + e <= M;
+        na[e] = ok ? an : (T)0;
+        nb[e] = (ok && n > 0) ? bn : (T)0;
+    }
+    st_vec<T>(oA, na);
+    st_vec<T>(oB, nb);
+    if (whole && n == 0)
+#pragma unroll
+        for (int e = 0; e < V; ++e) pn += (double)na[e];
+    if (whole && n == 1)
+#pragma unroll
+        for (int e = 0; e < V; ++e) pv += (double)nb[e];
+}
+
+/* split cluster barrier (all threads of every CTA of the cluster) */
+__device__ __forceinline__ void cluster_arrive() {
+    asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+
 /* global array a of a point: 0 a_w, 1 b_w, 2 a_f, 3 b_f */
 template <typename T>
 __device__ __forceinline__ T* gsel(const BatchInst<T>& I, int a) {
@@ -159,95 +221,110 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
 
         /* window accumulators (thread 0 of rank 0) */
         double acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0, acc4 = 0, acc5 = 0;
-        /* the four arrays of a CTA are contiguous, arr elements apart */
-        const T* nbr_up = rank > 0 ? cl.map_shared_rank(sAw, rank - 1) : sAw;
-        const T* nbr_dn = rank < C - 1 ? cl.map_shared_rank(sAw, rank + 1) : sAw;
+        /* neighbours' shared memory (the four arrays of a CTA are contiguous,
+         * arr elements apart): row r0-1 is the last row of rank-1 (its local
+         * row rows_per-1, shared row rows_per), row r1 the first row of
+         * rank+1 (shared row 1).  Rows outside 0..N read this CTA's own zero
+         * halo rows (shared rows 0 and R+1, never written). */
         const bool have_up = r0 >= 1 && R > 0, have_dn = r1 <= N && R > 0;
-        /* halo copy of arrays a0, a0+1 (0/1: whole grid, 2/3: fractional):
-         * row r0-1 is the last row of rank-1 (its local row rows_per-1),
-         * row r1 the first row of rank+1 (its local row 0) */
-        auto halo = [&](int a0) {
-            for (int q = tid; q < 4 * ncg; q += nthr) {
-                const int which = q / ncg, g = q - which * ncg;
-                const int a = a0 + (which & 1);
-                const bool up = which < 2;
-                if (up ? !have_up : !have_dn) continue;
-                const T* src = up ? nbr_up + a * arr + (size_t)rows_per * P
-                                  : nbr_dn + a * arr + (size_t)1 * P;
-                T* dst = sAw + a * arr + (up ? (size_t)0 : (size_t)(R + 1) * P);
-                T v[V];
-                ld_vec<T>(src + LG + g * V, v);
-                st_vec<T>(dst + LG + g * V, v);
-            }
-        };
+        const T* nbr_up = have_up ? cl.map_shared_rank(sAw, rank - 1) + (size_t)rows_per * P : sAw;
+        const T* nbr_dn = have_dn ? cl.map_shared_rank(sAw, rank + 1) + (size_t)P : sAw;
 
-        /* thread -> (column group, row phase), fixed for the point: a pass
-         * covers cpp consecutive column groups, rsplit rows at a time; every
-         * thread runs the same number of iterations (warp shuffles below) */
+        /* interior rows 1..R-2 read only this CTA's rows: thread -> (column
+         * group, row phase), fixed for the point; every thread runs the same
+         * number of iterations (the differences use warp shuffles) */
         const int cpp = min(ncg, nthr);
         const int rsplit = nthr / cpp;
         const int gl = tid % cpp, rp = tid / cpp;
         const bool t_on = rp < rsplit;
         const int npass = (ncg + cpp - 1) / cpp;
-        const int nrow = (R + rsplit - 1) / rsplit;
-        for (long long k = 0; k < K; ++k) {
-            const int kk = PP > 0 ? (int)(k % PP) : 0;
-            const T Ews = (T)I.e_whole[kk], Ewe = (T)I.e_whole[kk + 1];
-            const T Efs = (T)I.e_frac[kk], Efe = (T)I.e_frac[kk + 1];
-            double part_n = 0.0, part_v = 0.0;
-            /* ---- whole grid: z_w^{k+1} = T(z_w^k; S(z_f^{k+1/2})) ---- */
+        const int nint = R > 2 ? R - 2 : 0;
+        const int nrow = (nint + rsplit - 1) / rsplit;
+        /* boundary rows 0 and R-1 (one row when R == 1) */
+        const int nbnd = R >= 2 ? 2 : R;
+
+        /* one half-step on the rows of this CTA: own grid (o) updated in place
+         * from the other grid (x); `whole` selects the coefficients and the
+         * rows 0/1 sums */
+        auto half_interior = [&](int o, int x, const T (&E0)[V], const T (&E1)[V], bool whole,
+                                 double& pn, double& pv) {
             for (int pass = 0; pass < npass; ++pass) {
                 const int g = pass * cpp + gl;
                 const bool g_on = t_on && g < ncg;
                 const int m0 = (g_on ? g : 0) * V;
                 const bool l_adj = lane > 0 && gl > 0;
                 const bool r_adj = lane < 31 && gl + 1 < cpp && g + 1 < ncg;
-                T gc[V], ws[V], we[V];
+                T gc[V], t0[V], t1[V];
 #pragma unroll
                 for (int e = 0; e < V; ++e) {
                     const T bp = sBp[LG + m0 + e];
                     gc[e] = sG[LG + m0 + e];
-                    ws[e] = (Ews + bp) * hh;
-                    we[e] = (Ewe + bp) * hh;
+                    t0[e] = (E0[0] + bp) * hh;
+                    t1[e] = (E1[0] + bp) * hh;
                 }
                 for (int ii = 0; ii < nrow; ++ii) {
-                    const int i = rp + ii * rsplit;
-                    const bool on = g_on && i < R;
-                    const int il = on ? i : 0;
-                    const int n = r0 + il;
-                    const size_t o = (size_t)(il + 1) * P + LG + m0;
-                    T oa[V], ob[V], dfa_p1[V], dfa_m1[V], dfb_p1[V], dfb_m1[V];
-                    ld_vec<T>(sAw + o, oa);
-                    ld_vec<T>(sBw + o, ob);
-                    diff_sh<T>(sAf + o + P, l_adj, r_adj, dfa_p1);
-                    diff_sh<T>(sAf + o - P, l_adj, r_adj, dfa_m1);
-                    diff_sh<T>(sBf + o + P, l_adj, r_adj, dfb_p1);
-                    diff_sh<T>(sBf + o - P, l_adj, r_adj, dfb_m1);
+                    const int i = 1 + rp + ii * rsplit;
+                    const bool on = g_on && i < R - 1;
+                    const int il = on ? i : 1;
+                    const size_t c = (size_t)(il + 1) * P + LG + m0;
+                    T da_u[V], da_d[V], db_u[V], db_d[V];
+                    diff_sh<T>(sAw + x * arr + c - P, l_adj, r_adj, da_u);
+                    diff_sh<T>(sAw + x * arr + c + P, l_adj, r_adj, da_d);
+                    diff_sh<T>(sAw + (x + 1) * arr + c - P, l_adj, r_adj, db_u);
+                    diff_sh<T>(sAw + (x + 1) * arr + c + P, l_adj, r_adj, db_d);
                     if (!on) continue;
-                    const T nf = (T)n;
-                    const T chi = (n == 1) ? (T)2 : (T)1;
-                    const T ha0 = h * sR[il + 1];
-                    T wa[V], wb[V];
-#pragma unroll
-                    for (int e = 0; e < V; ++e) {
-                        T an, bn;
-                        cn_cell<T>(oa[e], ob[e], cc * (dfb_p1[e] - dfb_m1[e]),
-                                   cc * (chi * dfa_m1[e] - dfa_p1[e]), ha0 * gc[e], nf * ws[e],
-                                   nf * we[e], nu, xi, h, an, bn);
-                        const bool ok = m0 + e <= M;
-                        wa[e] = ok ? an : (T)0;
-                        wb[e] = (ok && n > 0) ? bn : (T)0;
-                    }
-                    st_vec<T>(sAw + o, wa);
-                    st_vec<T>(sBw + o, wb);
-                    if (n == 0)
-#pragma unroll
-                        for (int e = 0; e < V; ++e) part_n += (double)wa[e];
-                    if (n == 1)
-#pragma unroll
-                        for (int e = 0; e < V; ++e) part_v += (double)wb[e];
+                    cell_group<T>(sAw + o * arr + c, sAw + (o + 1) * arr + c, da_u, da_d, db_u,
+                                  db_d, r0 + il, m0, M, h * sR[il + 1], gc, t0, t1, nu, xi, h, cc,
+                                  whole, pn, pv);
                 }
             }
+        };
+        auto half_boundary = [&](int o, int x, const T (&E0)[V], const T (&E1)[V], bool whole,
+                                 double& pn, double& pv) {
+            for (int u = tid; u < nbnd * ncg; u += nthr) {
+                const int b = u / ncg, g = u - b * ncg;
+                const int il = b == 0 ? 0 : R - 1;
+                const int m0 = g * V;
+                const size_t c = (size_t)(il + 1) * P + LG + m0;
+                /* rows il-1 and il+1 of the other grid: local, or a neighbour's */
+                const T* up = (il == 0 && have_up) ? nbr_up + x * arr + LG + m0 : sAw + x * arr + c - P;
+                const T* dn = (il == R - 1 && have_dn) ? nbr_dn + x * arr + LG + m0
+                                                       : sAw + x * arr + c + P;
+                T da_u[V], da_d[V], db_u[V], db_d[V];
+                diff_ld<T>(up, da_u);
+                diff_ld<T>(dn, da_d);
+                diff_ld<T>(up + arr, db_u);
+                diff_ld<T>(dn + arr, db_d);
+                T gc[V], t0[V], t1[V];
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    const T bp = sBp[LG + m0 + e];
+                    gc[e] = sG[LG + m0 + e];
+                    t0[e] = (E0[0] + bp) * hh;
+                    t1[e] = (E1[0] + bp) * hh;
+                }
+                cell_group<T>(sAw + o * arr + c, sAw + (o + 1) * arr + c, da_u, da_d, db_u, db_d,
+                              r0 + il, m0, M, h * sR[il + 1], gc, t0, t1, nu, xi, h, cc, whole, pn,
+                              pv);
+            }
+        };
+
+        /* split cluster barriers: a CTA signals when its rows of one grid are
+         * complete, updates its interior rows of the other grid meanwhile,
+         * and waits only before the rows that read a neighbour */
+        cluster_arrive(); /* initial state loaded */
+        for (long long k = 0; k < K; ++k) {
+            const int kk = PP > 0 ? (int)(k % PP) : 0;
+            T Ew0[V], Ew1[V], Ef0[V], Ef1[V];
+            Ew0[0] = (T)I.e_whole[kk];
+            Ew1[0] = (T)I.e_whole[kk + 1];
+            Ef0[0] = (T)I.e_frac[kk];
+            Ef1[0] = (T)I.e_frac[kk + 1];
+            double part_n = 0.0, part_v = 0.0, dummy = 0.0;
+            /* ---- whole grid: z_w^{k+1} = T(z_w^k; S(z_f^{k+1/2})) ---- */
+            half_interior(0, 2, Ew0, Ew1, true, part_n, part_v);
+            cluster_wait();
+            half_boundary(0, 2, Ew0, Ew1, true, part_n, part_v);
             if (rank == 0) {
                 part_n = warp_sum(part_n);
                 part_v = warp_sum(part_v);
@@ -256,9 +333,8 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                     red[32 + warp] = part_v;
                 }
             }
-            cl.sync();
-            halo(0);
             __syncthreads();
+            cluster_arrive();
             if (rank == 0 && tid == 0) {
                 double sn = 0, sv = 0;
                 for (int w = 0; w < nwarp; ++w) {
@@ -280,57 +356,13 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                 acc5 = nn;
             }
             /* ---- fractional grid: z_f^{k+3/2} = T(z_f^{k+1/2}; S(z_w^{k+1})) ---- */
-            for (int pass = 0; pass < npass; ++pass) {
-                const int g = pass * cpp + gl;
-                const bool g_on = t_on && g < ncg;
-                const int m0 = (g_on ? g : 0) * V;
-                const bool l_adj = lane > 0 && gl > 0;
-                const bool r_adj = lane < 31 && gl + 1 < cpp && g + 1 < ncg;
-                T gc[V], fs[V], fe[V];
-#pragma unroll
-                for (int e = 0; e < V; ++e) {
-                    const T bp = sBp[LG + m0 + e];
-                    gc[e] = sG[LG + m0 + e];
-                    fs[e] = (Efs + bp) * hh;
-                    fe[e] = (Efe + bp) * hh;
-                }
-                for (int ii = 0; ii < nrow; ++ii) {
-                    const int i = rp + ii * rsplit;
-                    const bool on = g_on && i < R;
-                    const int il = on ? i : 0;
-                    const int n = r0 + il;
-                    const size_t o = (size_t)(il + 1) * P + LG + m0;
-                    T fa[V], fb[V], dwa_0[V], dwa_m2[V], dwb_0[V], dwb_m2[V];
-                    ld_vec<T>(sAf + o, fa);
-                    ld_vec<T>(sBf + o, fb);
-                    diff_sh<T>(sAw + o + P, l_adj, r_adj, dwa_0);
-                    diff_sh<T>(sAw + o - P, l_adj, r_adj, dwa_m2);
-                    diff_sh<T>(sBw + o + P, l_adj, r_adj, dwb_0);
-                    diff_sh<T>(sBw + o - P, l_adj, r_adj, dwb_m2);
-                    if (!on) continue;
-                    const T nf = (T)n;
-                    const T chi = (n == 1) ? (T)2 : (T)1;
-                    const T ha0 = h * sR[il + 1];
-                    T na[V], nb[V];
-#pragma unroll
-                    for (int e = 0; e < V; ++e) {
-                        T an, bn;
-                        cn_cell<T>(fa[e], fb[e], cc * (dwb_0[e] - dwb_m2[e]),
-                                   cc * (chi * dwa_m2[e] - dwa_0[e]), ha0 * gc[e], nf * fs[e],
-                                   nf * fe[e], nu, xi, h, an, bn);
-                        if (n == 0) bn = (T)0;
-                        const bool ok = m0 + e <= M;
-                        na[e] = ok ? an : (T)0;
-                        nb[e] = ok ? bn : (T)0;
-                    }
-                    st_vec<T>(sAf + o, na);
-                    st_vec<T>(sBf + o, nb);
-                }
-            }
-            cl.sync();
-            halo(2);
+            half_interior(2, 0, Ef0, Ef1, false, dummy, dummy);
+            cluster_wait();
+            half_boundary(2, 0, Ef0, Ef1, false, dummy, dummy);
             __syncthreads();
+            cluster_arrive();
         }
+        cluster_wait(); /* pairs the last arrive */
 
         /* ---- results: window sums, final state ---- */
         if (rank == 0 && tid == 0) {
@@ -350,7 +382,7 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
             st_vec<T>(gsel(I, a) + (size_t)(r0 + i) * gp + GG + g * V, v);
         }
         /* the next point's load overwrites shared memory that neighbours
-         * may still read in their last halo copy: wait for the cluster */
+         * may still read in their last boundary rows: wait for the cluster */
         cl.sync();
     }
 }
