@@ -222,20 +222,18 @@ int predict_chunks(bte_sur* h, const float* x_dev, long long n, float* mean, flo
     for (long long r0 = 0; r0 < n; r0 += h->cap) {
         const int rows = (int)std::min<long long>(h->cap, n - r0);
         const int Bp = round128(rows);
-        int rc = forward(h, x_dev, nullptr, r0, rows, Bp, false);
-        if (rc) return rc;
-        bte::sur::HeadArgs hd{};
-        hd.H3 = h->H3;
-        hd.params = h->p;
-        hd.pstride = h->pstride;
-        hd.oW4 = h->off.W4;
-        hd.ob4 = h->off.b4;
-        hd.Bp = Bp;
-        hd.H = h->H;
-        hd.nvalid = rows;
-        hd.Yh = h->Yh;
-        hd.sc = h->sc;
-        KL(bte::sur::launch_head(hd, h->M, h->stream));
+        bte::sur::InferArgs ia{};
+        ia.x = x_dev;
+        ia.row0 = r0;
+        ia.nvalid = rows;
+        ia.Bp = Bp;
+        ia.params = h->p;
+        ia.pstride = h->pstride;
+        ia.off = h->off;
+        ia.wb = h->wb;
+        ia.Yh = h->Yh;
+        ia.sc = h->sc;
+        KL(bte::sur::launch_infer(ia, h->M, h->stream));
         bte::sur::EnsArgs e{};
         e.Yh = h->Yh;
         e.members = h->M;

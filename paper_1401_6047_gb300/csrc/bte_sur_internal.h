@@ -141,6 +141,22 @@ struct AdamArgs {
     float lr, beta1, beta2, eps, c1, c2; /* c1 = 1/(1-beta1^t), c2 = 1/(1-beta2^t) */
 };
 
+/* Fused inference of every member (blockIdx.y) on 128 rows per CTA: the
+ * 5-input layer, both 256 x 256 layers (BF16 tensor cores, activations in
+ * shared memory) and the 2-output layer; writes Yh [M][Bp][2].  Rows r <
+ * nvalid read x[row0 + r]; H = 256. */
+struct InferArgs {
+    const float* x;
+    long long row0;
+    int nvalid, Bp;
+    const float* params;
+    long long pstride;
+    ParamOffsets off;
+    const __nv_bfloat16* wb; /* [M][2][H][H] */
+    float* Yh;
+    Scale sc;
+};
+
 struct EnsArgs {
     const float* Yh; /* [M][Bp][2] */
     int members, Bp, n;
@@ -159,6 +175,7 @@ int launch_reduce(const RedArgs& a, int members, void* stream);
 int launch_adam(const AdamArgs& a, void* stream);
 int launch_refresh_bf16(const AdamArgs& a, void* stream);
 int launch_ensemble(const EnsArgs& a, void* stream);
+int launch_infer(const InferArgs& a, int members, void* stream);
 /* number of values each 128-sample block writes in the reduction */
 int reduce_count(int H);
 
