@@ -654,7 +654,8 @@ def run_surrogate(args):
                       stream=stream.cuda_stream)
     sur.set_params(S.init_params(8, seed=0))
     t0 = time.perf_counter()
-    hist = sur.fit(x_tr, y_tr, **D.TRAINING)
+    # --no-train (profiling only): inference cost does not depend on the weights
+    hist = [float("nan")] if args.no_train else sur.fit(x_tr, y_tr, **D.TRAINING)
     train_s = time.perf_counter() - t0
 
     n = args.sur_points
@@ -776,10 +777,11 @@ def run_surrogate(args):
             "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
                          "frac": tflops / peak, "traffic": None,
                          "peak_source": "measured bf16_tflops (cuBLAS burst)",
-                         "kernel": "whole ensemble forward (5 kernels per 65,536-point chunk)",
+                         "kernel": "infer_tc_kernel (tcgen05; plus the ensemble mean/std kernel, "
+                                   "one of each per 65,536-point chunk)",
                          "flops_per_point": sur_flops_per_point()},
             "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 5 * (-(-n // 65536)) * args.steps, "clocks": clk,
+            "gpu_launches": (2 * (-(-n // 65536)) + 1) * args.steps, "clocks": clk,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -865,6 +867,8 @@ def main():
                     help="c4: points solved one by one for the single-instance comparison")
     ap.add_argument("--sur-points", dest="sur_points", type=int, default=1_000_000,
                     help="c5: points per inference step")
+    ap.add_argument("--no-train", dest="no_train", action="store_true",
+                    help="c5: skip training (profiling the inference kernels only)")
     ap.add_argument("--hybrid-sample", dest="hybrid_sample", type=int, default=256,
                     help="c5: held-out points timed through the surrogate with solver fallback")
     args = ap.parse_args()

@@ -34,6 +34,8 @@ struct bte_sur {
     unsigned char* mem;
     float *p, *g, *m, *v;
     bf16* wb;
+    bf16* wti; /* W2, W3 in the tensor cores' canonical layout (inference) */
+    int* err;
     float *Z1, *Z2, *Z3, *DY, *Yh, *partial;
     bf16 *H1, *H2, *H3, *DZ1, *DZ2, *DZ3;
     double* loss;
@@ -219,6 +221,7 @@ int round128(long long n) { return (int)((n + 127) / 128 * 128); }
 
 int predict_chunks(bte_sur* h, const float* x_dev, long long n, float* mean, float* stdv,
                    unsigned char* mask, double threshold) {
+    KL(bte::sur::launch_canon_weights(h->p, h->pstride, h->off, h->wti, h->M, h->stream));
     for (long long r0 = 0; r0 < n; r0 += h->cap) {
         const int rows = (int)std::min<long long>(h->cap, n - r0);
         const int Bp = round128(rows);
@@ -231,9 +234,11 @@ int predict_chunks(bte_sur* h, const float* x_dev, long long n, float* mean, flo
         ia.pstride = h->pstride;
         ia.off = h->off;
         ia.wb = h->wb;
+        ia.wti = h->wti;
         ia.Yh = h->Yh;
+        ia.err = h->err;
         ia.sc = h->sc;
-        KL(bte::sur::launch_infer(ia, h->M, h->stream));
+        KL(bte::sur::launch_infer_tc(ia, h->M, h->stream));
         bte::sur::EnsArgs e{};
         e.Yh = h->Yh;
         e.members = h->M;
@@ -298,6 +303,8 @@ int bte_sur_create(const bte_sur_config* cfg, bte_sur** out) {
     };
     const size_t op = take(P), og = take(P), om = take(P), ov = take(P);
     const size_t owb = take((size_t)M * 2 * H * H * 2);
+    const size_t owti = take((size_t)M * 2 * H * H * 2);
+    const size_t oerr = take(256);
     const size_t oz1 = take(act32), oz2 = take(act32), oz3 = take(act32);
     const size_t oh1 = take(act16), oh2 = take(act16), oh3 = take(act16);
     const size_t od1 = take(act16), od2 = take(act16), od3 = take(act16);
@@ -320,6 +327,8 @@ int bte_sur_create(const bte_sur_config* cfg, bte_sur** out) {
     h->m = (float*)(b + om);
     h->v = (float*)(b + ov);
     h->wb = (bf16*)(b + owb);
+    h->wti = (bf16*)(b + owti);
+    h->err = (int*)(b + oerr);
     h->Z1 = (float*)(b + oz1);
     h->Z2 = (float*)(b + oz2);
     h->Z3 = (float*)(b + oz3);
@@ -495,6 +504,9 @@ int bte_sur_predict(bte_sur* h, const float* x, int64_t n, float* mean, float* s
         if (mask) CU(cudaMemcpyAsync(mask + r0, h->mask_d, rows, cudaMemcpyDeviceToHost, h->stream));
         CU(cudaStreamSynchronize(h->stream));
     }
+    int err = 0;
+    CU(cudaMemcpy(&err, h->err, sizeof err, cudaMemcpyDeviceToHost));
+    if (err) return fail(BTE_ETIMEOUT, "a bounded wait in the inference kernel gave up");
     return BTE_OK;
 }
 

@@ -142,9 +142,9 @@ struct AdamArgs {
 };
 
 /* Fused inference of every member (blockIdx.y) on 128 rows per CTA: the
- * 5-input layer, both 256 x 256 layers (BF16 tensor cores, activations in
- * shared memory) and the 2-output layer; writes Yh [M][Bp][2].  Rows r <
- * nvalid read x[row0 + r]; H = 256. */
+ * 5-input layer, both 256 x 256 layers (tcgen05 tensor cores, activations
+ * in shared memory, accumulators in tensor memory) and the 2-output layer;
+ * writes Yh [M][Bp][2].  Rows r < nvalid read x[row0 + r]; H = 256. */
 struct InferArgs {
     const float* x;
     long long row0;
@@ -152,8 +152,10 @@ struct InferArgs {
     const float* params;
     long long pstride;
     ParamOffsets off;
-    const __nv_bfloat16* wb; /* [M][2][H][H] */
+    const __nv_bfloat16* wb;  /* [M][2][H][H] */
+    const __nv_bfloat16* wti; /* W2, W3 in the tensor cores' canonical layout */
     float* Yh;
+    int* err;                 /* set to 1 when a bounded wait gives up */
     Scale sc;
 };
 
@@ -175,7 +177,10 @@ int launch_reduce(const RedArgs& a, int members, void* stream);
 int launch_adam(const AdamArgs& a, void* stream);
 int launch_refresh_bf16(const AdamArgs& a, void* stream);
 int launch_ensemble(const EnsArgs& a, void* stream);
-int launch_infer(const InferArgs& a, int members, void* stream);
+/* tcgen05 inference (bte_sur_tc.cu) and the canonical-layout weight copy it reads */
+int launch_infer_tc(const InferArgs& a, int members, void* stream);
+int launch_canon_weights(const float* params, long long pstride, const ParamOffsets& off,
+                         __nv_bfloat16* wti, int members, void* stream);
 /* number of values each 128-sample block writes in the reduction */
 int reduce_count(int H);
 

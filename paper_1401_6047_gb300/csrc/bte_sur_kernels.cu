@@ -424,159 +424,9 @@ __global__ void ensemble_kernel(EnsArgs a) {
     if (a.mask) a.mask[r] = !(worst <= a.threshold);
 }
 
-/* ---- fused inference ---- */
-constexpr int IM = 128;           /* rows per CTA */
-constexpr int IH = 256;           /* hidden width */
-constexpr int IHP = IH + PAD;     /* padded activation row (bf16) */
-constexpr int IBN = 128;          /* output columns per pass */
-constexpr size_t kInferSmem =
-    2 * (size_t)IM * IHP * 2 + 2 * (size_t)IBN * (BK + PAD) * 2 + (size_t)IM * kIn * 4;
-
-__global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
-    extern __shared__ __align__(128) unsigned char ism[];
-    __nv_bfloat16* hA = reinterpret_cast<__nv_bfloat16*>(ism);
-    __nv_bfloat16* hB = hA + IM * IHP;
-    __nv_bfloat16* wr = hB + IM * IHP; /* [2][IBN][BK + PAD] weight chunks */
-    float* sx = reinterpret_cast<float*>(wr + 2 * IBN * (BK + PAD));
-    const int mem = blockIdx.y, r0 = blockIdx.x * IM;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float* P = a.params + mem * a.pstride;
-    const __nv_bfloat16* Wm = a.wb + (long long)mem * 2 * IH * IH;
-
-    for (int r = tid; r < IM; r += kThreads) {
-        float xh[kIn];
-        load_xh(a.x, nullptr, a.row0 + r0, r, a.nvalid - r0, a.sc, xh);
-#pragma unroll
-        for (int i = 0; i < kIn; ++i) sx[r * kIn + i] = xh[i];
-    }
-    __syncthreads();
-    /* layer 1 (K = 5): thread o computes unit o of every row */
-    {
-        const int o = tid;
-        float w[kIn];
-#pragma unroll
-        for (int i = 0; i < kIn; ++i) w[i] = P[a.off.W1 + (long long)o * kIn + i];
-        const float b = P[a.off.b1 + o];
-        for (int r = 0; r < IM; ++r) {
-            float z = b;
-#pragma unroll
-            for (int i = 0; i < kIn; ++i) z = fmaf(w[i], sx[r * kIn + i], z);
-            hA[r * IHP + o] = __float2bfloat16_rn(silu_f(z));
-        }
-    }
-    __syncthreads();
-
-    /* layers 2 and 3: h_out = silu(h_in W^T + b) on the tensor cores, the
-     * weights streamed through shared memory in 32-wide K chunks */
-    const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
-    const int g = lane >> 2, q = lane & 3, j = lane >> 3, rr = lane & 7;
-    for (int layer = 0; layer < 2; ++layer) {
-        const __nv_bfloat16* src = layer == 0 ? hA : hB;
-        __nv_bfloat16* dst = layer == 0 ? hB : hA;
-        const __nv_bfloat16* Wl = Wm + (long long)layer * IH * IH; /* [n][k] */
-        const float* bias = P + (layer == 0 ? a.off.b2 : a.off.b3);
-        for (int nh = 0; nh < IH / IBN; ++nh) {
-            float acc[4][4][4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) acc[i][jj][e] = 0.0f;
-            load_tile<false>(wr, Wl, IH, nh * IBN, 0);
-            cp_async_commit();
-            for (int kc = 0; kc < IH / BK; ++kc) {
-                const int st = kc & 1;
-                if (kc + 1 < IH / BK) load_tile<false>(wr + (st ^ 1) * IBN * (BK + PAD), Wl, IH, nh * IBN, (kc + 1) * BK);
-                cp_async_commit();
-                cp_async_wait<1>();
-                __syncthreads();
-                const __nv_bfloat16* tB = wr + st * IBN * (BK + PAD);
-#pragma unroll
-                for (int kk = 0; kk < BK; kk += 16) {
-                    uint32_t af[4][4];
-#pragma unroll
-                    for (int mi = 0; mi < 4; ++mi)
-                        ldsm_x4(af[mi], src + (wm + mi * 16 + (lane & 15)) * IHP + kc * BK + kk + (lane >> 4) * 8);
-                    uint32_t bf[4][2];
-#pragma unroll
-                    for (int ni = 0; ni < 4; ni += 2) {
-                        uint32_t t4[4];
-                        ldsm_x4(t4, tB + (wn + ni * 8 + (j >> 1) * 8 + rr) * (BK + PAD) + kk + (j & 1) * 8);
-                        bf[ni][0] = t4[0];
-                        bf[ni][1] = t4[1];
-                        bf[ni + 1][0] = t4[2];
-                        bf[ni + 1][1] = t4[3];
-                    }
-#pragma unroll
-                    for (int mi = 0; mi < 4; ++mi)
-#pragma unroll
-                        for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bf[ni][0], bf[ni][1]);
-                }
-                __syncthreads();
-            }
-#pragma unroll
-            for (int mi = 0; mi < 4; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int row = wm + mi * 16 + g + 8 * h;
-                        const int col = nh * IBN + wn + ni * 8 + 2 * q;
-                        const float z0 = acc[mi][ni][2 * h] + bias[col];
-                        const float z1 = acc[mi][ni][2 * h + 1] + bias[col + 1];
-                        *reinterpret_cast<__nv_bfloat162*>(dst + row * IHP + col) =
-                            __floats2bfloat162_rn(silu_f(z0), silu_f(z1));
-                    }
-        }
-        __syncthreads();
-    }
-
-    /* output layer (N = 2): one warp per row, lane l covers units 8l .. 8l+7 */
-    float w0[8], w1[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        w0[i] = P[a.off.W4 + lane * 8 + i];
-        w1[i] = P[a.off.W4 + IH + lane * 8 + i];
-    }
-    const float b40 = P[a.off.b4], b41 = P[a.off.b4 + 1];
-    for (int r = warp; r < IM; r += kThreads / 32) {
-        const uint4 raw = *reinterpret_cast<const uint4*>(hA + r * IHP + lane * 8);
-        const __nv_bfloat162* hp = reinterpret_cast<const __nv_bfloat162*>(&raw);
-        float y0 = 0.0f, y1 = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float2 f = __bfloat1622float2(hp[i]);
-            y0 = fmaf(w0[2 * i], f.x, y0);
-            y0 = fmaf(w0[2 * i + 1], f.y, y0);
-            y1 = fmaf(w1[2 * i], f.x, y1);
-            y1 = fmaf(w1[2 * i + 1], f.y, y1);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            y0 += __shfl_xor_sync(0xffffffffu, y0, o);
-            y1 += __shfl_xor_sync(0xffffffffu, y1, o);
-        }
-        if (lane == 0) {
-            const long long yo = ((long long)mem * a.Bp + r0 + r) * kOut;
-            a.Yh[yo] = y0 + b40;
-            a.Yh[yo + 1] = y1 + b41;
-        }
-    }
-}
-
 int ok_or(cudaError_t e) { return e == cudaSuccess ? 0 : (int)e; }
 
 }  // namespace
-
-int launch_infer(const InferArgs& a, int members, void* stream) {
-    cudaError_t e = cudaFuncSetAttribute(infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kInferSmem);
-    if (e != cudaSuccess) return (int)e;
-    const dim3 grid(a.Bp / IM, members);
-    infer_kernel<<<grid, kThreads, kInferSmem, (cudaStream_t)stream>>>(a);
-    return ok_or(cudaGetLastError());
-}
 
 int reduce_count(int H) { return red_count(H); }
 

@@ -1,0 +1,328 @@
+/*
+ * bte_sur_tc.cu -- ensemble inference of the surrogate MLP on the fifth-
+ * generation tensor cores (tcgen05, sm_103a).
+ *
+ * One CTA takes 128 rows of one member.  The 5-input layer runs on the FP32
+ * cores and writes h1 (BF16) into shared memory in the tensor cores'
+ * canonical K-major layout (8 x 8 core matrices, no swizzle).  Each 256 x 256
+ * layer is 2 x 16 tcgen05.mma instructions (M = 128, N = 128, K = 16, BF16
+ * in, FP32 accumulate) issued by one thread into 256 columns of tensor
+ * memory; the weight halves (64 KB each) arrive by bulk copy into two
+ * shared-memory buffers, the next layer's while the epilogue runs.  The
+ * epilogue reads the accumulators back (tcgen05.ld), adds the bias, applies
+ * SiLU and writes the next layer's BF16 operand in place.  The 2-output
+ * layer reads h3 from shared memory on the FP32 cores.
+ *
+ * Every wait on an mbarrier is bounded (about 2 s of %globaltimer); a wait
+ * that gives up sets the error word and the CTA still frees its tensor
+ * memory before it exits.
+ */
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "bte_device.cuh"
+#include "bte_sur_internal.h"
+
+namespace bte {
+namespace sur {
+namespace {
+
+constexpr int TM = 128;             /* rows per CTA (MMA M) */
+constexpr int TH = 256;             /* hidden width */
+constexpr int TN = 128;             /* MMA N (one weight half) */
+constexpr int TK = 16;              /* MMA K */
+constexpr int kThreadsTC = 256;
+constexpr uint32_t kHalfBytes = (uint32_t)TN * TH * 2; /* 64 KB */
+constexpr uint32_t kOpBytes = (uint32_t)TM * TH * 2;   /* 64 KB */
+constexpr uint32_t kCoreStride = 128;                  /* bytes of one 8 x 8 core matrix */
+constexpr uint32_t kGroupStride = (TH / 8) * kCoreStride; /* 4096: next 8-row group */
+/* dynamic shared memory: operand h, two weight halves, inputs, barriers */
+constexpr size_t kOffH = 0;
+constexpr size_t kOffW0 = kOffH + kOpBytes;
+constexpr size_t kOffW1 = kOffW0 + kHalfBytes;
+constexpr size_t kOffX = kOffW1 + kHalfBytes;
+constexpr size_t kOffBias = kOffX + (size_t)TM * kIn * 4; /* b2, b3 */
+constexpr size_t kOffBar = kOffBias + 2 * (size_t)TH * 4;
+constexpr size_t kSmemTC = kOffBar + 64 + 1024; /* + alignment slack */
+
+__device__ __forceinline__ float tanh_hw(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float silu_tc(float z) {
+    return z * fmaf(0.5f, tanh_hw(0.5f * z), 0.5f);
+}
+
+/* byte offset of element (r, k) of a [rows][256] K-major operand in the
+ * canonical no-swizzle layout */
+__host__ __device__ __forceinline__ uint32_t canon(int r, int k) {
+    return (uint32_t)(((r >> 3) * (TH / 8) + (k >> 3)) * kCoreStride + (r & 7) * 16 + (k & 7) * 2);
+}
+
+/* shared-memory matrix descriptor: start address, leading (K-direction
+ * core-matrix) byte offset, stride (8-row group) byte offset, descriptor
+ * version 1, no swizzle */
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+/* instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B,
+ * both K-major, N and M */
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+/* 32 lanes x 32 consecutive 32-bit columns: thread i gets row (lane base + i) */
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
+    extern __shared__ unsigned char tsm_raw[];
+    /* 1024-byte aligned base (descriptor addresses are 16-byte units) */
+    unsigned char* tsm = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(tsm_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char* hS = tsm + kOffH;
+    float* sx = reinterpret_cast<float*>(tsm + kOffX);
+    float* sb = reinterpret_cast<float*>(tsm + kOffBias);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tsm + kOffBar); /* w0, w1, mma */
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tsm + kOffBar + 32);
+    const uint32_t aH = dev::smem_u32(hS);
+    const uint32_t aW[2] = {dev::smem_u32(tsm + kOffW0), dev::smem_u32(tsm + kOffW1)};
+    const uint32_t bW[2] = {dev::smem_u32(&bars[0]), dev::smem_u32(&bars[1])};
+    const uint32_t bM = dev::smem_u32(&bars[2]);
+
+    const int mem = blockIdx.y, r0 = blockIdx.x * TM;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float* P = a.params + mem * a.pstride;
+    const unsigned char* Wg = reinterpret_cast<const unsigned char*>(a.wti) + (size_t)mem * 4 * kHalfBytes;
+    bool ok = true;
+
+    if (tid == 0) {
+        dev::mbar_init(bW[0], 1);
+        dev::mbar_init(bW[1], 1);
+        dev::mbar_init(bM, 1);
+        dev::fence_proxy_async_smem();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         dev::smem_u32(tmem_slot)),
+                     "r"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    /* weight halves of layer `l` into both buffers (4 bulk copies of 16 KB each) */
+    auto load_layer = [&](int l) {
+        for (int hh = 0; hh < 2; ++hh) {
+            dev::mbar_arrive_tx(bW[hh], kHalfBytes);
+            const unsigned char* src = Wg + (size_t)(2 * l + hh) * kHalfBytes;
+            for (int c = 0; c < 4; ++c)
+                dev::bulk_g2s(aW[hh] + c * (kHalfBytes / 4), src + c * (kHalfBytes / 4), kHalfBytes / 4,
+                              bW[hh]);
+        }
+    };
+    if (tid == 0) load_layer(0);
+    sb[tid] = P[a.off.b2 + tid]; /* TH == kThreadsTC */
+    sb[TH + tid] = P[a.off.b3 + tid];
+
+    /* ---- layer 1 on the FP32 cores: h1 = silu(W1 xh + b1) ---- */
+    for (int r = tid; r < TM; r += kThreadsTC) {
+        const int row = r0 + r;
+        float xh[kIn];
+        if (row < a.nvalid) {
+            const long long s = a.row0 + row;
+#pragma unroll
+            for (int i = 0; i < kIn; ++i)
+                xh[i] = 2.0f * (a.x[s * kIn + i] - a.sc.x_lo[i]) * a.sc.x_inv[i] - 1.0f;
+        } else {
+#pragma unroll
+            for (int i = 0; i < kIn; ++i) xh[i] = 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < kIn; ++i) sx[r * kIn + i] = xh[i];
+    }
+    __syncthreads();
+    {
+        const int o = tid; /* TH == kThreadsTC */
+        float w[kIn];
+#pragma unroll
+        for (int i = 0; i < kIn; ++i) w[i] = P[a.off.W1 + (long long)o * kIn + i];
+        const float b = P[a.off.b1 + o];
+        for (int r = 0; r < TM; ++r) {
+            float z = b;
+#pragma unroll
+            for (int i = 0; i < kIn; ++i) z = fmaf(w[i], sx[r * kIn + i], z);
+            *reinterpret_cast<__nv_bfloat16*>(hS + canon(r, o)) = __float2bfloat16_rn(silu_tc(z));
+        }
+    }
+
+    /* ---- layers 2 and 3 ---- */
+    constexpr uint32_t idesc = instr_desc(TM, TN);
+    const int sub = warp & 3;             /* TMEM lanes 32 sub .. 32 sub + 31 */
+    const int chalf = warp >> 2;          /* accumulator columns 128 chalf .. + 127 */
+    for (int l = 0; l < 2; ++l) {
+        /* operand written by the generic proxy -> visible to the tensor cores */
+        dev::fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            for (int hh = 0; hh < 2; ++hh)
+                if (!dev::mbar_wait(bW[hh], (uint32_t)l)) ok = false;
+            tc_fence_after();
+            for (int hh = 0; hh < 2; ++hh)
+                for (int ks = 0; ks < TH / TK; ++ks) {
+                    const uint64_t ad = smem_desc(aH + ks * 2 * kCoreStride, kCoreStride, kGroupStride);
+                    const uint64_t bd = smem_desc(aW[hh] + ks * 2 * kCoreStride, kCoreStride, kGroupStride);
+                    tc_mma(tmem + hh * TN, ad, bd, idesc, ks > 0 ? 1u : 0u);
+                }
+            tc_commit(bM);
+        }
+        if (!dev::mbar_wait(bM, (uint32_t)l)) ok = false;
+        tc_fence_after();
+        /* the weight buffers are free: fetch the next layer's */
+        if (tid == 0 && l == 0) load_layer(1);
+        /* epilogue: bias + SiLU, BF16, written as the next operand (row = TMEM lane) */
+        const float* bias = sb + l * TH;
+        const int row = sub * 32 + lane;
+        for (int cb = 0; cb < TN; cb += 32) {
+            const int col0 = chalf * TN + cb;
+            float v[32];
+            tc_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)col0, v);
+#pragma unroll
+            for (int c8 = 0; c8 < 32; c8 += 8) {
+                __nv_bfloat162 pk[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int col = col0 + c8 + 2 * e;
+                    pk[e] = __floats2bfloat162_rn(silu_tc(v[c8 + 2 * e] + bias[col]),
+                                                  silu_tc(v[c8 + 2 * e + 1] + bias[col + 1]));
+                }
+                *reinterpret_cast<uint4*>(hS + canon(row, col0 + c8)) = *reinterpret_cast<const uint4*>(pk);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+
+    /* ---- output layer (N = 2): one warp per row, lane c reads units 8c .. 8c+7 ---- */
+    float w0[8], w1[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        w0[i] = P[a.off.W4 + lane * 8 + i];
+        w1[i] = P[a.off.W4 + TH + lane * 8 + i];
+    }
+    const float b40 = P[a.off.b4], b41 = P[a.off.b4 + 1];
+    for (int r = warp; r < TM; r += kThreadsTC / 32) {
+        const uint4 raw = *reinterpret_cast<const uint4*>(hS + canon(r, lane * 8));
+        const __nv_bfloat162* hp = reinterpret_cast<const __nv_bfloat162*>(&raw);
+        float y0 = 0.0f, y1 = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 f = __bfloat1622float2(hp[i]);
+            y0 = fmaf(w0[2 * i], f.x, y0);
+            y0 = fmaf(w0[2 * i + 1], f.y, y0);
+            y1 = fmaf(w1[2 * i], f.x, y1);
+            y1 = fmaf(w1[2 * i + 1], f.y, y1);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+            y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+        }
+        if (lane == 0) {
+            const long long yo = ((long long)mem * a.Bp + r0 + r) * kOut;
+            a.Yh[yo] = y0 + b40;
+            a.Yh[yo + 1] = y1 + b41;
+        }
+    }
+    if (!ok) atomicExch(a.err, 1);
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256)
+                     : "memory");
+}
+
+/* W2, W3 of every member as BF16 in the canonical layout: [member][layer][half][128 x 256] */
+__global__ void canon_weights_kernel(const float* params, long long pstride, ParamOffsets off,
+                                     __nv_bfloat16* wti, int members) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long per = 2ll * TH * TH;
+    if (e >= per * members) return;
+    const int mem = (int)(e / per);
+    const long long q = e - mem * per;
+    const int l = (int)(q / (TH * TH));
+    const int n = (int)((q / TH) % TH), k = (int)(q % TH);
+    const float v = params[mem * pstride + (l == 0 ? off.W2 : off.W3) + (long long)n * TH + k];
+    unsigned char* dst = reinterpret_cast<unsigned char*>(wti) +
+                         ((size_t)mem * 4 + 2 * l + n / TN) * kHalfBytes + canon(n % TN, k);
+    *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
+}
+
+}  // namespace
+
+int launch_canon_weights(const float* params, long long pstride, const ParamOffsets& off,
+                         __nv_bfloat16* wti, int members, void* stream) {
+    const long long n = 2ll * TH * TH * members;
+    canon_weights_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        params, pstride, off, wti, members);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? 0 : (int)e;
+}
+
+int launch_infer_tc(const InferArgs& a, int members, void* stream) {
+    cudaError_t e = cudaFuncSetAttribute(infer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmemTC);
+    if (e != cudaSuccess) return (int)e;
+    const dim3 grid(a.Bp / TM, members);
+    infer_tc_kernel<<<grid, kThreadsTC, kSmemTC, (cudaStream_t)stream>>>(a);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? 0 : (int)e;
+}
+
+}  // namespace sur
+}  // namespace bte
