@@ -31,7 +31,7 @@ constexpr int TM = 128;             /* rows per CTA (MMA M) */
 constexpr int TH = 256;             /* hidden width */
 constexpr int TN = 128;             /* MMA N (one weight half) */
 constexpr int TK = 16;              /* MMA K */
-constexpr int kThreadsTC = 256;
+constexpr int kThreadsTC = 512; /* 16 warps: 4 per tensor-memory lane quadrant */
 constexpr uint32_t kHalfBytes = (uint32_t)TN * TH * 2; /* 64 KB */
 constexpr uint32_t kOpBytes = (uint32_t)TM * TH * 2;   /* 64 KB */
 constexpr uint32_t kCoreStride = 128;                  /* bytes of one 8 x 8 core matrix */
@@ -166,8 +166,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
         }
     };
     if (tid == 0) load_layer(0);
-    sb[tid] = P[a.off.b2 + tid]; /* TH == kThreadsTC */
-    sb[TH + tid] = P[a.off.b3 + tid];
+    if (tid < TH) {
+        sb[tid] = P[a.off.b2 + tid];
+        sb[TH + tid] = P[a.off.b3 + tid];
+    }
 
     /* ---- layer 1 on the FP32 cores: h1 = silu(W1 xh + b1) ---- */
     for (int r = tid; r < TM; r += kThreadsTC) {
@@ -187,12 +189,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
     }
     __syncthreads();
     {
-        const int o = tid; /* TH == kThreadsTC */
+        /* unit o of rows [64 rh, 64 rh + 64) */
+        const int o = tid & (TH - 1), rh = tid / TH;
         float w[kIn];
 #pragma unroll
         for (int i = 0; i < kIn; ++i) w[i] = P[a.off.W1 + (long long)o * kIn + i];
         const float b = P[a.off.b1 + o];
-        for (int r = 0; r < TM; ++r) {
+        for (int r = rh * (TM / 2); r < (rh + 1) * (TM / 2); ++r) {
             float z = b;
 #pragma unroll
             for (int i = 0; i < kIn; ++i) z = fmaf(w[i], sx[r * kIn + i], z);
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
     /* ---- layers 2 and 3 ---- */
     constexpr uint32_t idesc = instr_desc(TM, TN);
     const int sub = warp & 3;             /* TMEM lanes 32 sub .. 32 sub + 31 */
-    const int chalf = warp >> 2;          /* accumulator columns 128 chalf .. + 127 */
+    const int cq = warp >> 2;             /* accumulator columns 64 cq .. 64 cq + 63 */
     for (int l = 0; l < 2; ++l) {
         /* operand written by the generic proxy -> visible to the tensor cores */
         dev::fence_proxy_async_smem();
@@ -229,8 +232,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
         /* epilogue: bias + SiLU, BF16, written as the next operand (row = TMEM lane) */
         const float* bias = sb + l * TH;
         const int row = sub * 32 + lane;
-        for (int cb = 0; cb < TN; cb += 32) {
-            const int col0 = chalf * TN + cb;
+        for (int cb = 0; cb < TH / 4; cb += 32) {
+            const int col0 = cq * (TH / 4) + cb;
             float v[32];
             tc_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)col0, v);
 #pragma unroll
