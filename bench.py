@@ -387,7 +387,12 @@ def sweep_sample(args):
     an unbiased sample)."""
     from paper_1401_6047_gb300 import workloads as W
     prec = W.FP64 if args.precision == "fp64" else W.FP32_MIXED
-    pts = W.sweep_points(4096, precision=prec)
+    if args.periods:
+        # shortened runs (profiling): the grids and the mix of points stay the sweep's
+        pts = W.sweep_points(4096, precision=prec, periods=args.periods,
+                             avg_window=min(10.0, args.periods))
+    else:
+        pts = W.sweep_points(4096, precision=prec)
     n = max(1, min(4096, args.sweep_sample))
     stride = 4096 // n
     return pts[::stride][:n], stride
