@@ -381,10 +381,11 @@ SWEEP_DESC = ("batched sweep: seeded uniform E_dc in [0,6], E_omega in [0.01,1],
               "phi_y points by the grid rule; dt=1e-3, 30 periods, last 10 averaged")
 
 
-def sweep_sample(args):
+def sweep_sample(args, world: int = 1):
     """The 4096-point sweep and the bounded sample of it one step solves:
     every (4096 / n)-th point (the points are i.i.d. draws, so a stride is
-    an unbiased sample)."""
+    an unbiased sample), n = sweep_sample x ranks (weak scaling: the work
+    per GPU stays fixed)."""
     from paper_1401_6047_gb300 import workloads as W
     prec = W.FP64 if args.precision == "fp64" else W.FP32_MIXED
     if args.periods:
@@ -393,7 +394,7 @@ def sweep_sample(args):
                              avg_window=min(10.0, args.periods))
     else:
         pts = W.sweep_points(4096, precision=prec)
-    n = max(1, min(4096, args.sweep_sample))
+    n = max(1, min(4096, args.sweep_sample * world))
     stride = 4096 // n
     return pts[::stride][:n], stride
 
@@ -459,9 +460,11 @@ def run_sweep(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     from paper_1401_6047_gb300 import bte
 
-    allpts, stride = sweep_sample(args)
-    # weak scaling: rank r solves every world-th point of the sample
-    pts = allpts[rank::world] if world > 1 else allpts
+    allpts, stride = sweep_sample(args, world)
+    # weak scaling: the sample grows with the ranks; rank r solves its share
+    from paper_1401_6047_gb300 import shard
+    cost = [p.cells * bte.time_grid(p)[2] for p in allpts]
+    pts = [allpts[i] for i in shard.split(len(allpts), rank, world, cost)]
     elem = 8 if args.precision == "fp64" else 4
     vec = args.vec or (2 if elem == 8 else 4)
     tile = args.tile_m or 64 * vec
