@@ -220,7 +220,11 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
         __syncthreads();
 
         /* window accumulators (thread 0 of rank 0) */
-        double acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0, acc4 = 0, acc5 = 0;
+        /* window accumulators in shared memory (thread 0 of rank 0 only
+         * touches them; keeping them out of every thread's registers) */
+        double* acc = red + 64 + 2; /* [6], after the warp partials and s_next */
+        if (tid == 0)
+            for (int q = 0; q < 6; ++q) acc[q] = 0.0;
         /* neighbours' shared memory (the four arrays of a CTA are contiguous,
          * arr elements apart): row r0-1 is the last row of rank-1 (its local
          * row rows_per-1, shared row rows_per), row r1 the first row of
@@ -347,13 +351,13 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                     const double ang = PP > 0 ? 6.283185307179586476925286766559 *
                                                     (double)(k1 % PP) / (double)PP
                                               : I.omega * (double)k1 * I.dt_eff;
-                    acc0 += vv * cos(ang);
-                    acc1 += vv;
+                    acc[0] += vv * cos(ang);
+                    acc[1] += vv;
                 }
-                acc2 = fmax(acc2, fabs(nn - 1.0));
-                if (!isfinite(vv) || !isfinite(nn)) acc3 = 1.0;
-                acc4 = vv;
-                acc5 = nn;
+                acc[2] = fmax(acc[2], fabs(nn - 1.0));
+                if (!isfinite(vv) || !isfinite(nn)) acc[3] = 1.0;
+                acc[4] = vv;
+                acc[5] = nn;
             }
             /* ---- fractional grid: z_f^{k+3/2} = T(z_f^{k+1/2}; S(z_w^{k+1})) ---- */
             half_interior(2, 0, Ef0, Ef1, false, dummy, dummy);
@@ -366,12 +370,7 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
 
         /* ---- results: window sums, final state ---- */
         if (rank == 0 && tid == 0) {
-            I.acc[0] = acc0;
-            I.acc[1] = acc1;
-            I.acc[2] = acc2;
-            I.acc[3] = acc3;
-            I.acc[4] = acc4;
-            I.acc[5] = acc5;
+            for (int q = 0; q < 6; ++q) I.acc[q] = acc[q];
         }
         for (int q = tid; q < 4 * R * ncg; q += nthr) {
             const int a = q / (R * ncg);
@@ -399,7 +398,7 @@ size_t resident_smem_bytes(int N, int M, int C, size_t* arrays_bytes) {
     size_t b = (4 * arr + 2 * P + rows_per + 2) * sizeof(T);
     b = (b + 15) / 16 * 16;
     if (arrays_bytes) *arrays_bytes = b;
-    return b + 64 * sizeof(double) + 16;
+    return b + 64 * sizeof(double) + 16 + 6 * sizeof(double);
 }
 
 template <typename T>
