@@ -127,3 +127,19 @@ def test_sweep_sample_on_chip_matches_streamed():
     st = bte.batch_run(pts, resident=1)
     for o, r in zip(on, st):
         _agree(o, r, fp32=True)
+
+
+@pytest.mark.parametrize("prec,tol", [(W.FP64, 2e-6), (W.FP32_MIXED, 1e-5)])
+def test_absorption_spectrum_at_b0_matches_tucker(prec, tol):
+    """A(omega) spectrum shaped like the paper's B = 0 figure (mu = 50,
+    E_omega = 1, E_dc = 5, 24 frequencies) in one batched call, against the
+    closed form of Eq. absorption_def at B = 0 (tests/analytic.py), which
+    does not depend on mu; the drift average against its companion series."""
+    from tests import analytic as an
+    omegas = np.linspace(0.5, 12.0, 24)
+    pts = [W.surrogate_params([5.0, 1.0, w, 0.0, 50.0], prec) for w in omegas]
+    res = bte.batch_run(pts)
+    for w, p, o in zip(omegas, pts, res):
+        assert o.status == bte.OK
+        assert abs(o.absorption - an.tucker_absorption(5.0, 1.0, w)) <= tol, w
+        assert abs(o.v_dc_avg - an.tucker_vdc(5.0, 1.0, w, 50.0)) <= tol, w

@@ -73,6 +73,41 @@ def test_esaki_tsu():
     assert pin_esaki_tsu() <= 1
 
 
+def pin_b0_recurrence(flags=0):
+    """At B = 0 the stencil coefficient vanishes, so every cell of the whole
+    grid evolves on its own by the same 2x2 Crank-Nicolson map (Sec. 3,
+    Eqs. a_t_plus_1, b_t_plus_1 with the sign of b' that solves the system)
+    with theta independent of phi_y.  Summed over phi_y, the n = 1 harmonic
+    (A, B) = dphi sum_m (a_1m, b_1m) obeys that map with source h S, S =
+    dphi sum_m a0_1m, and the drift velocity is v_k = pi sqrt(alpha) B_k:
+    a two-variable recurrence that must match the 2-D oracle's whole trace
+    to roundoff."""
+    p = W.c1_fp64().replace(periods=2.0, avg_window=1.0, E_omega=0.7, E_dc=1.3)
+    r = oracle.solve(p, flags)
+    dt, P, K, Kw = oracle.time_grid(p)
+    a0 = oracle.equilibrium(p)
+    dphi = (p.phiy_max - p.phiy_min) / (p.m_points - 1)
+    S = dphi * a0[1].sum()
+    h = dt
+    nu, xi = 1 + h / 2, 1 - h / 2
+    E = lambda t: p.E_dc + p.E_omega * math.cos(p.omega * t)
+    A, Bv = S, 0.0
+    v = [0.0]
+    for k in range(K):
+        th, th1 = E(k * h) * h / 2, E((k + 1) * h) * h / 2
+        g = A * xi - Bv * th + h * S
+        q = Bv * xi + A * th
+        D = nu * nu + th1 * th1
+        A, Bv = (g * nu - q * th1) / D, (g * th1 + q * nu) / D
+        v.append(math.pi * math.sqrt(p.alpha) * Bv)
+    v = np.array(v)
+    return np.max(np.abs(r.v - v)) / (1e-13 * np.max(np.abs(v)))
+
+
+def test_b0_two_variable_recurrence():
+    assert pin_b0_recurrence() <= 1
+
+
 def pin_tucker(flags=0):
     """The 31 x 201 FP64 configuration (B = 0): absorption against the Tucker
     form and the time-averaged drift against its companion series.  The
@@ -315,12 +350,12 @@ def test_rejects_invalid_parameters():
 # --- every planted mistake is caught ----------------------------------------
 
 MUTATIONS = {
-    oracle.MUT_PAPER_B_SIGN: [pin_esaki_tsu],
+    oracle.MUT_PAPER_B_SIGN: [pin_esaki_tsu, pin_b0_recurrence],
     oracle.MUT_ALPHA_STENCIL: [pin_stationary, pin_characteristics],
     oracle.MUT_SIGMA0_ONE: [pin_equilibrium, pin_tucker],
     oracle.MUT_NO_CHI: [pin_stationary],
     oracle.MUT_STALE_SOURCE: [pin_order_dt],
-    oracle.MUT_THETA_START_ONLY: [pin_tucker],
+    oracle.MUT_THETA_START_ONLY: [pin_tucker, pin_b0_recurrence],
     oracle.MUT_STENCIL_INDEX: [pin_sublattice],
     oracle.MUT_NO_B0_RESET: [pin_stationary],
 }
