@@ -108,7 +108,7 @@ __device__ __forceinline__ void cell_group(T* oA, T* oB, const T (&da_u)[RV<T>::
                                            const T (&db_d)[RV<T>::V], int n, int m0, int M, T ha0,
                                            const T (&gc)[RV<T>::V], const T (&t0)[RV<T>::V],
                                            const T (&t1)[RV<T>::V], T nu, T xi, T h, T cc,
-                                           bool whole, double& pn, double& pv) {
+                                           bool whole, bool on, double& pn, double& pv) {
     constexpr int V = RV<T>::V;
     T oa[V], ob[V], na[V], nb[V];
     ld_vec<T>(oA, oa);
@@ -124,6 +124,7 @@ __device__ __forceinline__ void cell_group(T* oA, T* oB, const T (&da_u)[RV<T>::
         na[e] = ok ? an : (T)0;
         nb[e] = (ok && n > 0) ? bn : (T)0;
     }
+    if (!on) return;
     st_vec<T>(oA, na);
     st_vec<T>(oB, nb);
     if (whole && n == 0)
@@ -266,6 +267,9 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                     t0[e] = (E0[0] + bp) * hh;
                     t1[e] = (E1[0] + bp) * hh;
                 }
+                /* two rows in flight per thread (no branch between them, so the
+                 * second row's loads can issue during the first row's math) */
+#pragma unroll 2
                 for (int ii = 0; ii < nrow; ++ii) {
                     const int i = 1 + rp + ii * rsplit;
                     const bool on = g_on && i < R - 1;
@@ -276,10 +280,9 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                     diff_sh<T>(sAw + x * arr + c + P, l_adj, r_adj, da_d);
                     diff_sh<T>(sAw + (x + 1) * arr + c - P, l_adj, r_adj, db_u);
                     diff_sh<T>(sAw + (x + 1) * arr + c + P, l_adj, r_adj, db_d);
-                    if (!on) continue;
                     cell_group<T>(sAw + o * arr + c, sAw + (o + 1) * arr + c, da_u, da_d, db_u,
                                   db_d, r0 + il, m0, M, h * sR[il + 1], gc, t0, t1, nu, xi, h, cc,
-                                  whole, pn, pv);
+                                  whole, on, pn, pv);
                 }
             }
         };
@@ -308,8 +311,8 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                     t1[e] = (E1[0] + bp) * hh;
                 }
                 cell_group<T>(sAw + o * arr + c, sAw + (o + 1) * arr + c, da_u, da_d, db_u, db_d,
-                              r0 + il, m0, M, h * sR[il + 1], gc, t0, t1, nu, xi, h, cc, whole, pn,
-                              pv);
+                              r0 + il, m0, M, h * sR[il + 1], gc, t0, t1, nu, xi, h, cc, whole, true,
+                              pn, pv);
             }
         };
 
