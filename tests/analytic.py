@@ -110,3 +110,60 @@ def f0_fourier(mu: float, alpha: float, nmax: int, phiy: np.ndarray, nx: int = 1
     coef = np.concatenate([[c[0]], 2 * c[1:nmax + 1]])
     gy = np.sqrt(mu / (2 * np.pi * alpha)) * np.exp(-mu * phiy ** 2 / 2) / (2 * np.pi)
     return np.outer(coef, gy)
+
+
+def characteristics_ac(E_dc: float, E_omega: float, omega: float, B: float, mu: float,
+                       nphase: int = 12, nx: int = 64, ny: int = 96, ds: float = 0.01,
+                       smax: float = 25.0, ysig: float = 7.0):
+    """Periodic-state absorption and time-averaged drift velocity for the
+    drive E(t) = E_dc + E_omega cos(omega t) and constant B, by the method of
+    characteristics (the exact solution of the relaxation-time equation for
+    the divergence-free streaming field (E(t) + B phi_y, -B sin phi_x)):
+        v(t) = int_0^inf e^{-u} < sin Phi_x(t; t - u, phi0) >_{f0} du.
+    With tau = t - u and the period T = 2 pi/omega, the time averages become
+    averages over start phases tau in [0, T):
+        <v cos(omega t)> = (1/T) int_0^T dtau int_0^inf du e^{-u} cos(omega (tau + u)) G(tau, u)
+        <v>              = (1/T) int_0^T dtau int_0^inf du e^{-u} G(tau, u),
+    G(tau, u) = < sin Phi_x(tau + u; tau, phi0) >_{f0}.  Midpoint rule in tau
+    (periodic integrand), midpoint quadrature over phi0 (von Mises(mu) x
+    normal(0, 1/mu)), RK4 in u, Simpson in u.  Returns (A, v_dc) with
+    A = (2 I_0/I_1) <v cos(omega t)> (Eq. absorption_def)."""
+    T = 2 * np.pi / omega
+    tau = T * (np.arange(nphase) + 0.5) / nphase
+    x = 2 * np.pi * (np.arange(nx) + 0.5) / nx - np.pi
+    wx = np.exp(mu * (np.cos(x) - 1.0))
+    wx /= wx.sum()
+    L = ysig / np.sqrt(mu)
+    y = -L + 2 * L * (np.arange(ny) + 0.5) / ny
+    wy = np.exp(-mu * y * y / 2.0)
+    wy /= wy.sum()
+    w = np.outer(wx, wy)[None, :, :] / nphase
+    px = np.broadcast_to(x[None, :, None], (nphase, nx, ny)).copy()
+    py = np.broadcast_to(y[None, None, :], (nphase, nx, ny)).copy()
+    t0 = tau[:, None, None]
+
+    def f(px, py, u):
+        return E_dc + E_omega * np.cos(omega * (t0 + u)) + B * py, -B * np.sin(px)
+
+    ns = int(round(smax / ds))
+    ns += ns % 2
+    G = np.empty((ns + 1, nphase))
+    G[0] = np.sum(w * np.sin(px), axis=(1, 2))
+    for i in range(ns):
+        u = i * ds
+        k1 = f(px, py, u)
+        k2 = f(px + 0.5 * ds * k1[0], py + 0.5 * ds * k1[1], u + 0.5 * ds)
+        k3 = f(px + 0.5 * ds * k2[0], py + 0.5 * ds * k2[1], u + 0.5 * ds)
+        k4 = f(px + ds * k3[0], py + ds * k3[1], u + ds)
+        px = px + ds / 6 * (k1[0] + 2 * k2[0] + 2 * k3[0] + k4[0])
+        py = py + ds / 6 * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1])
+        G[i + 1] = np.sum(w * np.sin(px), axis=(1, 2))
+    u = ds * np.arange(ns + 1)
+    simpson = np.full(ns + 1, 2.0)
+    simpson[1::2] = 4.0
+    simpson[0] = simpson[-1] = 1.0
+    simpson *= ds / 3
+    decay = np.exp(-u)[:, None]
+    vc = np.sum(simpson[:, None] * decay * np.cos(omega * (tau[None, :] + u[:, None])) * G)
+    vb = np.sum(simpson[:, None] * decay * G)
+    return float(2.0 / bessel_ratio(mu, 1) * vc), float(vb)
