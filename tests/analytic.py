@@ -167,3 +167,49 @@ def characteristics_ac(E_dc: float, E_omega: float, omega: float, B: float, mu: 
     vc = np.sum(simpson[:, None] * decay * np.cos(omega * (tau[None, :] + u[:, None])) * G)
     vb = np.sum(simpson[:, None] * decay * G)
     return float(2.0 / bessel_ratio(mu, 1) * vc), float(vb)
+
+
+def f0_closed(phix, phiy, mu: float, alpha: float = 1.0):
+    """The equilibrium distribution (Eq. Bolzmann_initial_pdf):
+    f0 = sqrt(mu / (2 pi alpha)) exp(mu cos phi_x - mu phi_y^2 / 2) / (2 pi I_0(mu)),
+    written with exp(mu (cos - 1)) / ive(0, mu) to stay finite."""
+    return (np.sqrt(mu / (2 * np.pi * alpha)) * np.exp(mu * (np.cos(phix) - 1.0) - mu * phiy ** 2 / 2)
+            / (2 * np.pi * sp.ive(0, mu)))
+
+
+def characteristics_pdf(E_dc: float, E_omega: float, omega: float, B: float, mu: float,
+                        t: float, phix, phiy, alpha: float = 1.0, ds: float = 1e-3):
+    """The distribution f(phi_x, phi_y, t) of the relaxation-time equation
+    started from f0 at t = 0, by backward characteristics: with Phi(t'; t,
+    phi) the trajectory of the streaming field (E(t') + B phi_y, -B sin
+    phi_x) through phi at time t,
+        f(phi, t) = e^{-t} f0(Phi(0)) + int_0^t e^{-s} f0(Phi(t - s)) ds.
+    RK4 backward in time, Simpson in s (t / ds even)."""
+    px = np.array(phix, dtype=np.float64)
+    py = np.array(phiy, dtype=np.float64)
+    ns = int(round(t / ds))
+    ns += ns % 2
+    ds = t / ns
+
+    def f(px, py, tt):  # d phi / d t' (the backward step uses -ds)
+        return E_dc + E_omega * np.cos(omega * tt) + B * py, -B * np.sin(px)
+
+    vals = [f0_closed(px, py, mu, alpha)]
+    tt = t
+    for i in range(ns):
+        h = -ds
+        k1 = f(px, py, tt)
+        k2 = f(px + 0.5 * h * k1[0], py + 0.5 * h * k1[1], tt + 0.5 * h)
+        k3 = f(px + 0.5 * h * k2[0], py + 0.5 * h * k2[1], tt + 0.5 * h)
+        k4 = f(px + h * k3[0], py + h * k3[1], tt + h)
+        px = px + h / 6 * (k1[0] + 2 * k2[0] + 2 * k3[0] + k4[0])
+        py = py + h / 6 * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1])
+        tt += h
+        vals.append(f0_closed(px, py, mu, alpha))
+    vals = np.array(vals)  # vals[i]: f0 at Phi(t - i ds)
+    s = ds * np.arange(ns + 1)
+    wts = np.full(ns + 1, 2.0)
+    wts[1::2] = 4.0
+    wts[0] = wts[-1] = 1.0
+    integral = ds / 3 * np.tensordot(wts * np.exp(-s), vals, axes=1)
+    return np.exp(-t) * vals[-1] + integral

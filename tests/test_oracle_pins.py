@@ -349,6 +349,45 @@ def test_characteristics_ac_at_finite_B():
     assert pin_characteristics_ac() <= 1
 
 
+def _f_from_harmonics(a, b, phix, m_idx):
+    """f = sum_n a_n cos(n phi_x) + b_n sin(n phi_x) (Eq. f_fourier) at
+    (phi_x, column m) pairs."""
+    n = np.arange(a.shape[0])
+    return np.array([np.sum(a[:, m] * np.cos(n * x) + b[:, m] * np.sin(n * x))
+                     for x, m in zip(phix, m_idx)])
+
+
+def pin_pdf_characteristics(flags=0):
+    """The whole distribution, pointwise: f(phi_x, phi_y, t ~ 1) summed from
+    the oracle's harmonics (B != 0, time-dependent drive, alpha != 1),
+    Richardson-extrapolated in dphi, against backward characteristics from
+    the closed-form f0 (tests/analytic.py) at 12 random points."""
+    rng = np.random.default_rng(3)
+    fs = []
+    for mp in (321, 641):
+        p = W.Params(E_dc=1.0, E_omega=0.5, omega=2.0, B=1.0, mu=3.0, alpha=0.9496, n_max=24,
+                     m_points=mp, phiy_min=-8, phiy_max=8, dt=2e-3, periods=1.0,
+                     avg_window=1.0)
+        dt, P, K, Kw = oracle.time_grid(p)
+        k = int(round(1.0 / dt))
+        st = oracle.init(p, flags)
+        oracle.advance(p, st, 0, k, flags)
+        # the same physical points on both grids (columns of the coarse grid)
+        rng = np.random.default_rng(3)
+        mc = rng.integers(80, 240, 12)
+        m_idx = mc * (mp - 1) // 320
+        phix = rng.uniform(-math.pi, math.pi, 12)
+        fs.append(_f_from_harmonics(st.aw, st.bw, phix, m_idx))
+    phiy = -8 + mc * (16.0 / 320)
+    f_ex = fs[1] - (fs[0] - fs[1]) / 3.0
+    ref = an.characteristics_pdf(1.0, 0.5, 2.0, 1.0, 3.0, k * dt, phix, phiy, alpha=0.9496)
+    return np.max(np.abs(f_ex - ref)) / (2e-5 * np.max(np.abs(ref)))
+
+
+def test_pdf_pointwise_against_characteristics():
+    assert pin_pdf_characteristics() <= 1
+
+
 # --- window arithmetic -------------------------------------------------------
 
 def test_window_of_pure_cosine():
@@ -378,12 +417,13 @@ def test_rejects_invalid_parameters():
 
 MUTATIONS = {
     oracle.MUT_PAPER_B_SIGN: [pin_esaki_tsu, pin_b0_recurrence],
-    oracle.MUT_ALPHA_STENCIL: [pin_stationary, pin_characteristics, pin_characteristics_ac],
+    oracle.MUT_ALPHA_STENCIL: [pin_stationary, pin_characteristics, pin_characteristics_ac,
+                               pin_pdf_characteristics],
     oracle.MUT_SIGMA0_ONE: [pin_equilibrium, pin_tucker],
-    oracle.MUT_NO_CHI: [pin_stationary],
+    oracle.MUT_NO_CHI: [pin_stationary, pin_pdf_characteristics],
     oracle.MUT_STALE_SOURCE: [pin_order_dt],
     oracle.MUT_THETA_START_ONLY: [pin_tucker, pin_b0_recurrence, pin_characteristics_ac],
-    oracle.MUT_STENCIL_INDEX: [pin_sublattice],
+    oracle.MUT_STENCIL_INDEX: [pin_sublattice, pin_pdf_characteristics],
     oracle.MUT_NO_B0_RESET: [pin_stationary],
 }
 
