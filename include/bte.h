@@ -165,6 +165,14 @@ BTE_API int bte_set_state(bte_handle* h, int grid, const double* a, const double
  * resume from a checkpoint. */
 BTE_API int bte_set_step(bte_handle* h, int64_t k, const double* v, const double* norm);
 
+/* The distribution itself, f(phi_x, phi_y) = sum_{n=0}^{n_max} a_n(phi_y)
+ * cos(n phi_x) + b_n(phi_y) sin(n phi_x) (Sec. 2, Eq. f_fourier; a_0 holds
+ * the sigma_0 = 1/2 factor), of one grid (0 = whole grid at step k, 1 =
+ * fractional grid) on nphix phi_x points -pi + 2 pi i / nphix (i = 0 ..
+ * nphix-1) times the m_points phi_y grid, evaluated on the GPU in FP64:
+ * HOST out [nphix][m_points].  1 <= nphix <= 65535; synchronises. */
+BTE_API int bte_pdf(bte_handle* h, int grid, int32_t nphix, double* out);
+
 /* Frees the handle and everything it allocated.  NULL is ignored. */
 BTE_API void bte_destroy(bte_handle* h);
 

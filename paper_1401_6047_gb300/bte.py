@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
             "bte_get_state": ([vp, ctypes.c_int, dp, dp], ctypes.c_int),
             "bte_set_state": ([vp, ctypes.c_int, dp, dp], ctypes.c_int),
             "bte_set_step": ([vp, i64, dp, dp], ctypes.c_int),
+            "bte_pdf": ([vp, ctypes.c_int, ctypes.c_int32, dp], ctypes.c_int),
             "bte_destroy": ([vp], None),
             "bte_last_error": ([], ctypes.c_char_p),
             "bte_bessel_ratio": ([ctypes.c_double, ctypes.c_int32, dp], ctypes.c_int),
@@ -280,6 +281,13 @@ class Solver:
         b = np.ascontiguousarray(b, dtype=np.float64)
         assert a.shape == self.shape and b.shape == self.shape
         _check(self._lib.bte_set_state(self._h, int(grid), _dp(a), _dp(b)))
+
+    def pdf(self, grid: int = 0, nphix: int = 128) -> np.ndarray:
+        """f(phi_x, phi_y) of one grid on nphix x m_points points
+        (``bte_pdf``); phi_x = -pi + 2 pi i / nphix."""
+        out = np.zeros((int(nphix), self.shape[1]))
+        _check(self._lib.bte_pdf(self._h, int(grid), int(nphix), _dp(out)))
+        return out
 
     def set_step(self, k: int, v: np.ndarray, norm: np.ndarray) -> None:
         v = np.ascontiguousarray(v, dtype=np.float64)

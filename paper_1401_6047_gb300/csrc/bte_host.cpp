@@ -1332,6 +1332,29 @@ int bte_set_step(bte_handle* h, int64_t k, const double* v, const double* norm) 
     return BTE_OK;
 }
 
+int bte_pdf(bte_handle* h, int grid, int32_t nphix, double* out) {
+    if (!h || (grid != 0 && grid != 1) || !out || nphix < 1 || nphix > 65535)
+        return fail(BTE_EINVAL, "bad argument (grid 0/1, 1 <= nphix <= 65535)");
+    const Layout& L = h->L;
+    const int set = h->set, M1 = h->p.m_points;
+    const size_t bytes = (size_t)nphix * M1 * sizeof(double);
+    double* d = nullptr;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BTE_ENOMEM, "pdf buffer of %zu bytes", bytes);
+    }
+    const size_t oa = L.off_state[4 * set + 2 * grid], ob = L.off_state[4 * set + 2 * grid + 1];
+    int r = h->fp64 ? bte::launch_pdf<double>(h->ptr<double>(oa), h->ptr<double>(ob), h->p.n_max,
+                                              M1 - 1, L.pitch, nphix, d, h->stream)
+                    : bte::launch_pdf<float>(h->ptr<float>(oa), h->ptr<float>(ob), h->p.n_max,
+                                             M1 - 1, L.pitch, nphix, d, h->stream);
+    cudaError_t e = r ? (cudaError_t)r : cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(BTE_ECUDA, "pdf: %s", cudaGetErrorString(e));
+    return BTE_OK;
+}
+
 void bte_destroy(bte_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);

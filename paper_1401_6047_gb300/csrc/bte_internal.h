@@ -153,6 +153,10 @@ int launch_observe(const T* a_w, const T* b_w, int M, int pitch, double vscale,
                    void* stream);
 int launch_advance_base(long long* base, long long by, void* stream);
 int launch_finalize(const FinalArgs& a, void* stream);
+/* f on an nphix x (M+1) grid from the harmonics of one grid: out [nphix][M+1] (device) */
+template <typename T>
+int launch_pdf(const T* a, const T* b, int N, int M, int pitch, int nphix, double* out,
+               void* stream);
 /* On-chip batched kernel: shared memory a CTA needs for a point of N+1
  * harmonics and M+1 columns split over C CTAs (*arrays_bytes: the part
  * before the warp partials), clusters that fit the GPU at once, launch. */

@@ -132,6 +132,30 @@ __global__ void finalize_kernel(FinalArgs A) {
     }
 }
 
+/* f(phi_x_i, phi_y_m) = sum_n a_n(m) cos(n phi_x_i) + b_n(m) sin(n phi_x_i)
+ * (Eq. f_fourier), phi_x_i = -pi + 2 pi i / nphix; one thread per (i, m),
+ * cos / sin of n phi_x by the rotation recurrence, FP64 sums. */
+template <typename T>
+__global__ void pdf_kernel(const T* a, const T* b, int N, int M, int pitch, int nphix,
+                           double* out) {
+    constexpr int G = Cols<T>::G;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (m > M || i >= nphix) return;
+    const double x = -3.14159265358979323846 + 6.28318530717958647692 * (double)i / (double)nphix;
+    double s1, c1;
+    sincos(x, &s1, &c1);
+    double c = 1.0, s = 0.0, f = 0.0;
+    for (int n = 0; n <= N; ++n) {
+        const size_t q = (size_t)n * pitch + G + m;
+        f += (double)a[q] * c + (double)b[q] * s;
+        const double cn = c * c1 - s * s1;
+        s = s * c1 + c * s1;
+        c = cn;
+    }
+    out[(size_t)i * (M + 1) + m] = f;
+}
+
 }  // namespace
 
 /* ---------------------------------------------------------------------- */
@@ -172,11 +196,20 @@ int launch_finalize(const FinalArgs& a, void* stream) {
     return ok_or(cudaGetLastError());
 }
 
+template <typename T>
+int launch_pdf(const T* a, const T* b, int N, int M, int pitch, int nphix, double* out,
+               void* stream) {
+    const dim3 grid((M + 1 + 127) / 128, nphix);
+    pdf_kernel<T><<<grid, 128, 0, (cudaStream_t)stream>>>(a, b, N, M, pitch, nphix, out);
+    return ok_or(cudaGetLastError());
+}
+
 #define BTE_INSTANTIATE(T)                                                                     \
     template int launch_init<T>(T*, T*, const T*, const T*, int, int, int, void*);             \
     template int launch_apply<T>(const ApplyArgs<T>&, void*);                                  \
     template int launch_observe<T>(const T*, const T*, int, int, double, double, double*,      \
-                                   double*, long long, void*);
+                                   double*, long long, void*);                                 \
+    template int launch_pdf<T>(const T*, const T*, int, int, int, int, double*, void*);
 BTE_INSTANTIATE(float)
 BTE_INSTANTIATE(double)
 
