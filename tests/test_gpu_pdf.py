@@ -47,8 +47,8 @@ def test_pdf_equals_host_sum_and_integrates_to_observables(prec):
 
 def test_pdf_pointwise_against_characteristics():
     """t ~ 1 from the equilibrium, B != 0 and a time-dependent drive: the GPU
-    distribution on the 641-point grid within 5e-5 (relative to its
-    maximum) of backward characteristics (the error is O(dphi^2))."""
+    distribution on the 641-point grid within 5e-5 of its maximum of
+    backward characteristics at 16 random points (the error is O(dphi^2))."""
     p = W.Params(E_dc=1.0, E_omega=0.5, omega=2.0, B=1.0, mu=3.0, alpha=0.9496, n_max=24,
                  m_points=641, phiy_min=-8, phiy_max=8, dt=2e-3, periods=1.0, avg_window=1.0,
                  precision=W.FP64)
@@ -64,7 +64,7 @@ def test_pdf_pointwise_against_characteristics():
     x = -math.pi + 2 * math.pi * i / nphix
     y = p.phiy_min + m * (p.phiy_max - p.phiy_min) / (p.m_points - 1)
     ref = an.characteristics_pdf(1.0, 0.5, 2.0, 1.0, 3.0, k * dt, x, y, alpha=0.9496)
-    assert np.max(np.abs(f[i, m] - ref)) <= 5e-5 * np.max(np.abs(ref))
+    assert np.max(np.abs(f[i, m] - ref)) <= 5e-5 * np.max(np.abs(f))
 
 
 def test_pdf_dump_is_a_readable_image(tmp_path):
