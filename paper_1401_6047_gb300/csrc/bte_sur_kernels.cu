@@ -23,14 +23,10 @@ constexpr int PAD = 8;        /* bf16 elements of row padding (16 bytes) */
 /* one stage: the larger of the [128][32+8] and [32][128+8] tile shapes */
 constexpr int kTileElems = (BM * (BK + PAD) > BK * (BM + PAD)) ? BM * (BK + PAD) : BK * (BM + PAD);
 
-/* sigmoid(z) = (1 + tanh(z/2)) / 2 with the hardware tanh approximation
- * (relative error ~2^-11, below the bfloat16 rounding that follows) */
-__device__ __forceinline__ float tanh_hw(float x) {
-    float y;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float sigmoid_f(float z) { return fmaf(0.5f, tanh_hw(0.5f * z), 0.5f); }
+/* sigmoid(z) = 1 / (1 + exp(-z)) with the fast exponential and reciprocal
+ * (relative error ~1e-7, so the bfloat16 rounding that follows matches an
+ * exact evaluation; exp(-z) = inf gives 0) */
+__device__ __forceinline__ float sigmoid_f(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
 __device__ __forceinline__ float silu_f(float z) { return z * sigmoid_f(z); }
 __device__ __forceinline__ float silu_grad_f(float z) {
     const float s = sigmoid_f(z);

@@ -45,14 +45,8 @@ constexpr size_t kOffBias = kOffX + (size_t)TM * kIn * 4; /* b2, b3 */
 constexpr size_t kOffBar = kOffBias + 2 * (size_t)TH * 4;
 constexpr size_t kSmemTC = kOffBar + 64 + 1024; /* + alignment slack */
 
-__device__ __forceinline__ float tanh_hw(float x) {
-    float y;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float silu_tc(float z) {
-    return z * fmaf(0.5f, tanh_hw(0.5f * z), 0.5f);
-}
+/* silu(z) = z / (1 + exp(-z)), fast exponential and reciprocal (as in training) */
+__device__ __forceinline__ float silu_tc(float z) { return z * __fdividef(1.0f, 1.0f + __expf(-z)); }
 
 /* byte offset of element (r, k) of a [rows][256] K-major operand in the
  * canonical no-swizzle layout */
