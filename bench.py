@@ -478,6 +478,16 @@ def run_sweep(args):
     kw = dict(tile_m=tile, chunk_n=chunk, vec=vec, graph_steps=args.graph_steps,
               max_batch=max_batch, max_batch_bytes=max_bytes, stream=stream.cuda_stream,
               resident=args.resident, resident_smem=args.resident_smem)
+    tuned = None
+    if args.tune:
+        # the library's autotuner on the same points (shortened runs), before timing
+        t0 = time.perf_counter()
+        best, secs = bte.batch_tune(pts, sample=16, steps=2000,
+                                    **{k: v for k, v in kw.items() if k != "stream"})
+        tuned = {"options": best, "seconds": time.perf_counter() - t0,
+                 "candidate_seconds": [None if s > 1e299 else s for s in secs.tolist()]}
+        kw.update(best)
+        tile, chunk, vec = kw["tile_m"] or tile, kw["chunk_n"] or chunk, kw["vec"] or vec
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         res = bte.batch_run(pts, **kw)
@@ -584,7 +594,7 @@ def run_sweep(args):
                                  "over the whole batch solve, against HBM for comparison with the "
                                  "streamed tier; the on-chip tier keeps the state in shared memory "
                                  "and moves no HBM bytes per step"},
-            "cpu_baseline": cpu, "single_instance_gpu": single, "e2e": e2e,
+            "cpu_baseline": cpu, "single_instance_gpu": single, "e2e": e2e, "tuned": tuned,
             "gpu_launches": launches * args.steps, "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -866,6 +876,8 @@ def main():
     ap.add_argument("--sweep-sample", dest="sweep_sample", type=int, default=256,
                     help="c4: points of the 4096-point sweep solved per step")
     ap.add_argument("--max-batch", dest="max_batch", type=int, default=0)
+    ap.add_argument("--tune", action="store_true",
+                    help="c4: pick the batched-run options with the library's autotuner first")
     ap.add_argument("--resident", type=int, default=0,
                     help="c4: 0 on chip where a point fits, 1 never, 2 only")
     ap.add_argument("--resident-smem", dest="resident_smem", type=int, default=0,

@@ -261,6 +261,20 @@ BTE_API int bte_batch_run(const bte_params* p, int32_t n, bte_obs* out,
 BTE_API int bte_batch_plan(const bte_params* p, int32_t n, const bte_batch_opts* opts,
                            int32_t* tier);
 
+/* Autotuner of bte_batch_run's options for a set of points.  Takes
+ * `sample` of the points (evenly spaced in cost order, cost = cells x
+ * steps), shortens their runs so that the longest has about `steps` time
+ * steps (relative run lengths kept), and times bte_batch_run on them for 12
+ * candidate option sets (each run once untimed, then timed): on-chip tier
+ * with 232,448 / 160,000 / 113,664 bytes of shared memory per CTA, then the
+ * streamed tier alone with tile_m = {32, 64, 128} x vec and chunk_n = {8, 16,
+ * 32}.  *best receives the fastest (fields not tuned copied from *base,
+ * which may be NULL); seconds (HOST, 12 values, may be NULL) the time of each
+ * candidate in that order (1e300 where a candidate does not apply).
+ * Synchronous; uses the GPU. */
+BTE_API int bte_batch_tune(const bte_params* p, int32_t n, const bte_batch_opts* base,
+                           int32_t sample, int32_t steps, bte_batch_opts* best, double* seconds);
+
 /* Library version string. */
 BTE_API const char* bte_version(void);
 

@@ -106,6 +106,8 @@ def lib() -> ctypes.CDLL:
                                ctypes.POINTER(bte_batch_opts)], ctypes.c_int),
             "bte_batch_plan": ([P, ctypes.c_int32, ctypes.POINTER(bte_batch_opts),
                                 ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+            "bte_batch_tune": ([P, ctypes.c_int32, ctypes.POINTER(bte_batch_opts), ctypes.c_int32,
+                                ctypes.c_int32, ctypes.POINTER(bte_batch_opts), dp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -323,6 +325,24 @@ def batch_plan(points, **opts) -> np.ndarray:
     _check(lib().bte_batch_plan(arr, n, ctypes.byref(o),
                                 tier.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
     return tier[:n]
+
+
+TUNE_FIELDS = ("tile_m", "chunk_n", "vec", "graph_steps", "max_batch", "max_batch_bytes",
+               "resident", "resident_smem")
+
+
+def batch_tune(points, sample: int = 16, steps: int = 2000, **opts):
+    """``bte_batch_tune``: (best options as a dict of batch_run keywords,
+    seconds of the 12 candidates)."""
+    pts = list(points)
+    n = len(pts)
+    arr = (bte_params * n)(*[to_params(q) for q in pts])
+    base = _batch_opts(**opts)
+    best = bte_batch_opts()
+    secs = np.zeros(12)
+    _check(lib().bte_batch_tune(arr, n, ctypes.byref(base), int(sample), int(steps),
+                                ctypes.byref(best), secs.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return {k: int(getattr(best, k)) for k in TUNE_FIELDS}, secs
 
 
 def batch_run(points, tile_m: int = 0, chunk_n: int = 0, vec: int = 0, graph_steps: int = 0,

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1088,6 +1089,99 @@ int bte_batch_plan(const bte_params* p, int32_t n, const bte_batch_opts* opts, i
     const int rc = batch_prepare(p, n, opts, pts, cfg);
     if (rc) return rc;
     for (const BatchPoint& b : pts) tier[b.idx] = b.resC;
+    return BTE_OK;
+}
+
+int bte_batch_tune(const bte_params* p, int32_t n, const bte_batch_opts* base, int32_t sample,
+                   int32_t steps, bte_batch_opts* best, double* seconds) {
+    if (!p || !best || n < 1 || sample < 1 || steps < 2)
+        return fail(BTE_EINVAL, "bte_batch_tune: bad argument");
+    bte_batch_opts b0;
+    if (base) b0 = *base;
+    else std::memset(&b0, 0, sizeof b0);
+    {
+        std::vector<BatchPoint> pts;
+        BatchCfg cfg;
+        const int rc = batch_prepare(p, n, &b0, pts, cfg); /* validates every point */
+        if (rc) return rc;
+    }
+    /* the sample: points evenly spaced in cost order, runs shortened to about
+     * `steps` steps (relative run lengths kept) */
+    std::vector<std::pair<double, int>> cost(n);
+    for (int i = 0; i < n; ++i) {
+        TimeGrid tg;
+        time_grid(&p[i], tg);
+        cost[i] = {(double)(p[i].n_max + 1) * p[i].m_points * tg.K, i};
+    }
+    std::sort(cost.begin(), cost.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
+        return a.first != b.first ? a.first > b.first : a.second < b.second;
+    });
+    const int ns = std::min(sample, n);
+    long long Kmax = 0;
+    for (int i = 0; i < n; ++i) {
+        TimeGrid tg;
+        time_grid(&p[i], tg);
+        Kmax = std::max(Kmax, tg.K);
+    }
+    const double scale = std::min(1.0, (double)steps / (double)Kmax);
+    std::vector<bte_params> sp(ns);
+    for (int j = 0; j < ns; ++j) {
+        bte_params q = p[cost[(size_t)j * n / ns].second];
+        if (q.omega > 0) {
+            const double Pd = std::nearbyint(kTwoPi / (q.omega * q.dt)); /* steps per period */
+            q.periods = std::max(q.periods * scale, 2.0 / Pd);
+            if (q.avg_window > q.periods) q.avg_window = q.periods;
+        } else {
+            q.t_max = std::max(q.t_max * scale, 2.0 * q.dt);
+            if (q.avg_window > q.t_max) q.avg_window = q.t_max;
+        }
+        sp[j] = q;
+    }
+    /* candidates: on-chip budgets, then streamed shapes */
+    const bool fp64 = p[0].precision == BTE_FP64;
+    const int v = b0.vec ? b0.vec : (fp64 ? 2 : 4);
+    std::vector<bte_batch_opts> cand;
+    for (int smem : {232448, 160000, 113664}) {
+        bte_batch_opts o = b0;
+        o.resident = 0;
+        o.resident_smem = smem;
+        cand.push_back(o);
+    }
+    for (int tw : {32, 64, 128})
+        for (int ch : {8, 16, 32}) {
+            bte_batch_opts o = b0;
+            o.resident = 1;
+            o.tile_m = tw * v;
+            o.chunk_n = ch;
+            cand.push_back(o);
+        }
+    std::vector<bte_obs> out(ns);
+    double best_t = 1e300;
+    int best_i = -1;
+    for (size_t c = 0; c < cand.size(); ++c) {
+        double t = 1e300;
+        std::vector<BatchPoint> chk;
+        BatchCfg cfg;
+        if (batch_prepare(sp.data(), ns, &cand[c], chk, cfg) == BTE_OK) {
+            /* the first run builds graphs and warms caches; the second is timed */
+            int rc = bte_batch_run(sp.data(), ns, out.data(), &cand[c]);
+            if (rc == BTE_OK || rc == BTE_EUNSTABLE) {
+                const auto t0 = std::chrono::steady_clock::now();
+                rc = bte_batch_run(sp.data(), ns, out.data(), &cand[c]);
+                const auto t1 = std::chrono::steady_clock::now();
+                if (rc == BTE_OK || rc == BTE_EUNSTABLE) t = std::chrono::duration<double>(t1 - t0).count();
+            }
+            if (rc == BTE_ECUDA || rc == BTE_ENOMEM || rc == BTE_ETIMEOUT) return rc;
+        }
+        if (seconds) seconds[c] = t;
+        if (t < best_t) {
+            best_t = t;
+            best_i = (int)c;
+        }
+    }
+    if (best_i < 0) return fail(BTE_EINVAL, "no candidate launch shape ran");
+    *best = cand[best_i];
+    g_err.clear();
     return BTE_OK;
 }
 

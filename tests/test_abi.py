@@ -124,3 +124,14 @@ def test_batch_plan_assigns_tiers_on_host():
     with pytest.raises(bte.BteError) as e:
         bte.batch_plan(pts, resident=2)
     assert e.value.code == bte.EINVAL
+
+
+def test_batch_tune_rejects_bad_arguments_on_host():
+    pts = [W.c1_fp64()]
+    for kw in (dict(sample=0), dict(steps=1)):
+        with pytest.raises(bte.BteError) as e:
+            bte.batch_tune(pts, **kw)
+        assert e.value.code == bte.EINVAL
+    with pytest.raises(bte.BteError) as e:
+        bte.batch_tune([W.c1_fp64().replace(m_points=2)])
+    assert e.value.code == bte.EINVAL

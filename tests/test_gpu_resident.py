@@ -143,3 +143,19 @@ def test_absorption_spectrum_at_b0_matches_tucker(prec, tol):
         assert o.status == bte.OK
         assert abs(o.absorption - an.tucker_absorption(5.0, 1.0, w)) <= tol, w
         assert abs(o.v_dc_avg - an.tucker_vdc(5.0, 1.0, w, 50.0)) <= tol, w
+
+
+def test_autotuner_returns_the_fastest_valid_options():
+    pts = _points(W.FP32_MIXED, seed=53, n=10)
+    best, secs = bte.batch_tune(pts, sample=6, steps=300)
+    assert secs.shape == (12,)
+    finite = secs[secs < 1e299]
+    assert finite.size >= 6
+    i = int(np.argmin(secs))
+    # the returned options are the fastest candidate's, and they run
+    expect_resident = 0 if i < 3 else 1
+    assert best["resident"] == expect_resident
+    res = bte.batch_run(pts, **best)
+    ref = bte.batch_run(pts, resident=1)
+    for o, r in zip(res, ref):
+        _agree(o, r, fp32=True)
