@@ -100,15 +100,14 @@ __device__ __forceinline__ void diff_ld(const T* p, T (&d)[RV<T>::V]) {
  * da_u, da_d, db_u, db_d the phi_y differences of the other grid's a and b
  * in rows n-1 (u) and n+1 (d); t0, t1 the drive/field factors
  * (E + B phi_m) dt/4 at the start and end of the half-step.  Same
- * expressions as the streaming kernel.  With `whole`, adds row 0's a and
- * row 1's b to the norm / drift sums. */
+ * expressions as the streaming kernel. */
 template <typename T>
 __device__ __forceinline__ void cell_group(T* oA, T* oB, const T (&da_u)[RV<T>::V],
                                            const T (&da_d)[RV<T>::V], const T (&db_u)[RV<T>::V],
                                            const T (&db_d)[RV<T>::V], int n, int m0, int M, T ha0,
                                            const T (&gc)[RV<T>::V], const T (&t0)[RV<T>::V],
                                            const T (&t1)[RV<T>::V], T nu, T xi, T h, T cc,
-                                           bool whole, bool on, double& pn, double& pv) {
+                                           bool on) {
     constexpr int V = RV<T>::V;
     T oa[V], ob[V], na[V], nb[V];
     ld_vec<T>(oA, oa);
@@ -127,12 +126,6 @@ __device__ __forceinline__ void cell_group(T* oA, T* oB, const T (&da_u)[RV<T>::
     if (!on) return;
     st_vec<T>(oA, na);
     st_vec<T>(oB, nb);
-    if (whole && n == 0)
-#pragma unroll
-        for (int e = 0; e < V; ++e) pn += (double)na[e];
-    if (whole && n == 1)
-#pragma unroll
-        for (int e = 0; e < V; ++e) pv += (double)nb[e];
 }
 
 /* split cluster barrier (all threads of every CTA of the cluster) */
@@ -236,8 +229,14 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
         const T* nbr_dn = have_dn ? cl.map_shared_rank(sAw, rank + 1) + (size_t)P : sAw;
 
         /* interior rows 1..R-2 read only this CTA's rows: thread -> (column
-         * group, row phase), fixed for the point; every thread runs the same
-         * number of iterations (the differences use warp shuffles) */
+         * group gl, row block rp), fixed for the point.  A block of nrow
+         * consecutive rows [lo, lo + nrow) is walked as two chains of stride
+         * 2 (lo, lo+2, ... then lo+1, lo+3, ...): the other grid's
+         * differences of row i+1 serve rows i and i+2, so each chain loads
+         * one other-grid row per row it updates, plus one at its start.  Every
+         * thread runs the same number of iterations (the differences use
+         * warp shuffles); iterations past row R-2 read clamped rows and store
+         * nothing. */
         const int cpp = min(ncg, nthr);
         const int rsplit = nthr / cpp;
         const int gl = tid % cpp, rp = tid / cpp;
@@ -245,14 +244,13 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
         const int npass = (ncg + cpp - 1) / cpp;
         const int nint = R > 2 ? R - 2 : 0;
         const int nrow = (nint + rsplit - 1) / rsplit;
+        const int lo = 1 + rp * nrow;
         /* boundary rows 0 and R-1 (one row when R == 1) */
         const int nbnd = R >= 2 ? 2 : R;
 
         /* one half-step on the rows of this CTA: own grid (o) updated in place
-         * from the other grid (x); `whole` selects the coefficients and the
-         * rows 0/1 sums */
-        auto half_interior = [&](int o, int x, const T (&E0)[V], const T (&E1)[V], bool whole,
-                                 double& pn, double& pv) {
+         * from the other grid (x) */
+        auto half_interior = [&](int o, int x, const T (&E0)[V], const T (&E1)[V]) {
             for (int pass = 0; pass < npass; ++pass) {
                 const int g = pass * cpp + gl;
                 const bool g_on = t_on && g < ncg;
@@ -267,27 +265,40 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                     t0[e] = (E0[0] + bp) * hh;
                     t1[e] = (E1[0] + bp) * hh;
                 }
-                /* two rows in flight per thread (no branch between them, so the
-                 * second row's loads can issue during the first row's math) */
-#pragma unroll 2
-                for (int ii = 0; ii < nrow; ++ii) {
-                    const int i = 1 + rp + ii * rsplit;
-                    const bool on = g_on && i < R - 1;
-                    const int il = on ? i : 1;
-                    const size_t c = (size_t)(il + 1) * P + LG + m0;
-                    T da_u[V], da_d[V], db_u[V], db_d[V];
-                    diff_sh<T>(sAw + x * arr + c - P, l_adj, r_adj, da_u);
-                    diff_sh<T>(sAw + x * arr + c + P, l_adj, r_adj, da_d);
-                    diff_sh<T>(sAw + (x + 1) * arr + c - P, l_adj, r_adj, db_u);
-                    diff_sh<T>(sAw + (x + 1) * arr + c + P, l_adj, r_adj, db_d);
-                    cell_group<T>(sAw + o * arr + c, sAw + (o + 1) * arr + c, da_u, da_d, db_u,
-                                  db_d, r0 + il, m0, M, h * sR[il + 1], gc, t0, t1, nu, xi, h, cc,
-                                  whole, on, pn, pv);
+                const T* xa = sAw + x * arr + LG + m0; /* other grid, shared row 0 */
+                for (int ch = 0; ch < 2; ++ch) {
+                    const int len = (nrow + 1 - ch) / 2; /* same for every thread */
+                    if (len == 0) continue;             /* also when R < 3 */
+                    const int i0 = lo + ch;
+                    /* differences of the other grid's row i0-1 (shared row i0) */
+                    T da_u[V], db_u[V];
+                    {
+                        const int il = min(i0, R - 2);
+                        diff_sh<T>(xa + (size_t)il * P, l_adj, r_adj, da_u);
+                        diff_sh<T>(xa + arr + (size_t)il * P, l_adj, r_adj, db_u);
+                    }
+#pragma unroll 1
+                    for (int ii = 0; ii < len; ++ii) {
+                        const int i = i0 + 2 * ii;
+                        const bool on = g_on && i < R - 1;
+                        const int il = min(i, R - 2);
+                        T da_d[V], db_d[V];
+                        diff_sh<T>(xa + (size_t)(il + 2) * P, l_adj, r_adj, da_d);
+                        diff_sh<T>(xa + arr + (size_t)(il + 2) * P, l_adj, r_adj, db_d);
+                        const size_t c = (size_t)(il + 1) * P + LG + m0;
+                        cell_group<T>(sAw + o * arr + c, sAw + (o + 1) * arr + c, da_u, da_d, db_u,
+                                      db_d, r0 + il, m0, M, h * sR[il + 1], gc, t0, t1, nu, xi, h,
+                                      cc, on);
+#pragma unroll
+                        for (int e = 0; e < V; ++e) {
+                            da_u[e] = da_d[e];
+                            db_u[e] = db_d[e];
+                        }
+                    }
                 }
             }
         };
-        auto half_boundary = [&](int o, int x, const T (&E0)[V], const T (&E1)[V], bool whole,
-                                 double& pn, double& pv) {
+        auto half_boundary = [&](int o, int x, const T (&E0)[V], const T (&E1)[V]) {
             for (int u = tid; u < nbnd * ncg; u += nthr) {
                 const int b = u / ncg, g = u - b * ncg;
                 const int il = b == 0 ? 0 : R - 1;
@@ -311,14 +322,17 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                     t1[e] = (E1[0] + bp) * hh;
                 }
                 cell_group<T>(sAw + o * arr + c, sAw + (o + 1) * arr + c, da_u, da_d, db_u, db_d,
-                              r0 + il, m0, M, h * sR[il + 1], gc, t0, t1, nu, xi, h, cc, whole, true,
-                              pn, pv);
+                              r0 + il, m0, M, h * sR[il + 1], gc, t0, t1, nu, xi, h, cc, true);
             }
         };
 
         /* split cluster barriers: a CTA signals when its rows of one grid are
          * complete, updates its interior rows of the other grid meanwhile,
-         * and waits only before the rows that read a neighbour */
+         * and waits only before the rows that read a neighbour.  Rank 0 adds
+         * the new whole grid's rows 0 (a) and 1 (b) while the fractional
+         * half-step runs (that half-step leaves the whole grid unchanged);
+         * thread 0 folds the warp partials into the window sums after the
+         * step's last block barrier. */
         cluster_arrive(); /* initial state loaded */
         for (long long k = 0; k < K; ++k) {
             const int kk = PP > 0 ? (int)(k % PP) : 0;
@@ -327,19 +341,37 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
             Ew1[0] = (T)I.e_whole[kk + 1];
             Ef0[0] = (T)I.e_frac[kk];
             Ef1[0] = (T)I.e_frac[kk + 1];
-            double part_n = 0.0, part_v = 0.0, dummy = 0.0;
             /* ---- whole grid: z_w^{k+1} = T(z_w^k; S(z_f^{k+1/2})) ---- */
-            half_interior(0, 2, Ew0, Ew1, true, part_n, part_v);
+            half_interior(0, 2, Ew0, Ew1);
             cluster_wait();
-            half_boundary(0, 2, Ew0, Ew1, true, part_n, part_v);
+            half_boundary(0, 2, Ew0, Ew1);
+            __syncthreads();
+            cluster_arrive();
             if (rank == 0) {
-                part_n = warp_sum(part_n);
-                part_v = warp_sum(part_v);
+                /* local rows 0 and 1 are shared rows 1 and 2; without a row 1
+                 * (N = 0) shared row 2 is a zero halo row */
+                double pn = 0.0, pv = 0.0;
+                for (int g = tid; g < ncg; g += nthr) {
+                    T va[V], vb[V];
+                    ld_vec<T>(sAw + P + LG + g * V, va);
+                    ld_vec<T>(sBw + 2 * P + LG + g * V, vb);
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        pn += (double)va[e];
+                        pv += (double)vb[e];
+                    }
+                }
+                pn = warp_sum(pn);
+                pv = warp_sum(pv);
                 if (lane == 0) {
-                    red[warp] = part_n;
-                    red[32 + warp] = part_v;
+                    red[warp] = pn;
+                    red[32 + warp] = pv;
                 }
             }
+            /* ---- fractional grid: z_f^{k+3/2} = T(z_f^{k+1/2}; S(z_w^{k+1})) ---- */
+            half_interior(2, 0, Ef0, Ef1);
+            cluster_wait();
+            half_boundary(2, 0, Ef0, Ef1);
             __syncthreads();
             cluster_arrive();
             if (rank == 0 && tid == 0) {
@@ -362,12 +394,6 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                 acc[4] = vv;
                 acc[5] = nn;
             }
-            /* ---- fractional grid: z_f^{k+3/2} = T(z_f^{k+1/2}; S(z_w^{k+1})) ---- */
-            half_interior(2, 0, Ef0, Ef1, false, dummy, dummy);
-            cluster_wait();
-            half_boundary(2, 0, Ef0, Ef1, false, dummy, dummy);
-            __syncthreads();
-            cluster_arrive();
         }
         cluster_wait(); /* pairs the last arrive */
 
