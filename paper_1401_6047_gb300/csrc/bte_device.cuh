@@ -76,14 +76,17 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-/* 1/x for the Crank-Nicolson denominator D = nu^2 + theta'^2 >= 1: the fast
- * single-precision intrinsic in FP32 (D never approaches the intrinsic's
- * special ranges), the correctly rounded division in FP64. */
+/* 1/x for the Crank-Nicolson denominator D = nu^2 + theta'^2 >= 1: the
+ * hardware approximate reciprocal in FP32 (PTX rcp.approx.ftz.f32, about one
+ * ulp; D is never subnormal, zero or infinite), the correctly rounded
+ * division in FP64. */
 template <typename T>
 __device__ __forceinline__ T recip(T x);
 template <>
 __device__ __forceinline__ float recip<float>(float x) {
-    return __fdividef(1.0f, x);
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 template <>
 __device__ __forceinline__ double recip<double>(double x) {
