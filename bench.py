@@ -72,9 +72,13 @@ def measured_peaks():
 
 
 def kernel_sha() -> str:
-    src = os.path.join(ROOT, "paper_1401_6047_gb300", "csrc", "bte_step.cu")
-    with open(src, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the step kernel's sources (the kernel file and the device
+    helpers and shared declarations it includes)."""
+    h = hashlib.sha256()
+    for name in ("bte_step.cu", "bte_device.cuh", "bte_internal.h"):
+        with open(os.path.join(ROOT, "paper_1401_6047_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(config_key: str):
