@@ -67,7 +67,7 @@ typedef enum {
 /* Problem parameters (dimensionless units of Sec. 2, Eqs. substitutions). */
 typedef struct {
     double E_dc, E_omega, omega; /* drive E(t) = E_dc + E_omega cos(omega t)   */
-    double B;                    /* magnetic field                             */
+    double B;                    /* magnetic field: its constant part          */
     double mu;                   /* Delta_1 / (2 k_B T), > 0                   */
     double alpha;                /* m / m_x, > 0 (observables do not depend on it) */
     double phiy_min, phiy_max;   /* phi_y grid, both ends included             */
@@ -81,6 +81,15 @@ typedef struct {
     int32_t m_points;            /* phi_y points M+1, >= 3                      */
     int32_t precision;           /* bte_precision                               */
     int32_t reserved;            /* must be 0                                   */
+    /* Time-dependent field B(t) = B + B_omega cos(omega t + B_phase), at the
+     * drive's frequency (constant B + B_omega cos(B_phase) when omega == 0).
+     * Eqs. a_n_dot and b_n_dot hold for any B(t) (Sec. 2); the scheme samples
+     * B where it samples E: the rotation n (E + B phi_y) of a half-step at
+     * its start and its end, the stencil coefficient B dt/(4 dphi) at the
+     * time of the other grid that supplies the stencil (the middle of the
+     * half-step; t = 0 for the start-up half step).  Zero for the paper's
+     * constant field. */
+    double B_omega, B_phase;
 } bte_params;
 
 /* Observables (Sec. 2, Eqs. v_dr_generic, norm_in_phi, absorption_def). */

@@ -30,6 +30,7 @@ MUT_STALE_SOURCE = 16
 MUT_THETA_START_ONLY = 32
 MUT_STENCIL_INDEX = 64
 MUT_NO_B0_RESET = 128
+MUT_B_STENCIL_START = 256
 
 
 class _Params(ctypes.Structure):
@@ -42,6 +43,7 @@ class _Params(ctypes.Structure):
         ("t_max", ctypes.c_double), ("avg_window", ctypes.c_double),
         ("n_max", ctypes.c_int32), ("m_points", ctypes.c_int32),
         ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("B_omega", ctypes.c_double), ("B_phase", ctypes.c_double),
     ]
 
 
@@ -108,6 +110,8 @@ def _params(p, flags: int = 0) -> _Params:
     s.n_max = int(g("n_max"))
     s.m_points = int(g("m_points"))
     s.flags = int(flags)
+    s.B_omega = float(g("B_omega", 0.0))
+    s.B_phase = float(g("B_phase", 0.0))
     return s
 
 

@@ -39,6 +39,12 @@
  *      periods (rectangle rule on a periodic signal).
  *   R8 integrals over phi_y are dphi * sum over the M+1 grid points.
  *   R9 observables are taken from the whole grid at integer steps.
+ *   R13 a time-dependent field B(t) (Sec. 2 notes that Eqs. a_n_dot, b_n_dot
+ *      allow one; here B(t) = B + B_omega cos(omega t + B_phase)) is sampled
+ *      like E: the rotation mu, mu' takes B at the start and the end of the
+ *      (half-)step, the stencil coefficient B dt/(4 dphi) takes B at the time
+ *      of the grid that supplies the stencil (the middle of the half-step; 0
+ *      for the start-up half step, whose source is the initial state).
  *
  * Parity pins: every function here is pinned by tests that do not use this
  * file's arithmetic (closed forms at B = 0, Esaki-Tsu, Tucker, relaxation,
@@ -72,6 +78,7 @@ typedef struct {
     int32_t m_points;   /* phi_y grid points M+1                              */
     int32_t flags;      /* planted mistakes, 0 = the method                   */
     int32_t reserved;
+    double B_omega, B_phase; /* B(t) = B + B_omega cos(omega t + B_phase)     */
 } oracle_params;
 
 enum {
@@ -82,7 +89,8 @@ enum {
     ORACLE_MUT_STALE_SOURCE = 16,     /* fractional step reads the old whole grid */
     ORACLE_MUT_THETA_START_ONLY = 32, /* theta' evaluated at the step start    */
     ORACLE_MUT_STENCIL_INDEX = 64,    /* off-by-one column in one S^a term     */
-    ORACLE_MUT_NO_B0_RESET = 128      /* keep the n = 0 b update               */
+    ORACLE_MUT_NO_B0_RESET = 128,     /* keep the n = 0 b update               */
+    ORACLE_MUT_B_STENCIL_START = 256  /* stencil coefficient from B at t0      */
 };
 
 } /* extern "C" */
@@ -107,7 +115,7 @@ int check_params(const oracle_params* p) {
     if (!p) return -1;
     const double v[] = {p->E_dc, p->E_omega, p->omega, p->B, p->mu, p->alpha,
                         p->phiy_min, p->phiy_max, p->dt, p->periods, p->t_max,
-                        p->avg_window};
+                        p->avg_window, p->B_omega, p->B_phase};
     for (double x : v)
         if (!std::isfinite(x)) return -1;
     if (p->n_max < 1 || p->m_points < 3) return -1;
@@ -190,6 +198,11 @@ double E_at(const oracle_params* p, double t) {
     return p->E_dc + p->E_omega * std::cos(p->omega * t);
 }
 
+double B_at(const oracle_params* p, double t) {
+    /* reading R13: B(t) = B + B_omega cos(omega t + B_phase); B for the paper */
+    return p->B + p->B_omega * std::cos(p->omega * t + p->B_phase);
+}
+
 /* Value of a grid array at (n, m); zero outside the computed region
  * (boundary conditions Eqs. a_boundary and b_boundary). */
 inline double at(const double* x, const Grid& g, int n, int m) {
@@ -202,28 +215,31 @@ inline double at_b(const double* x, const Grid& g, int n, int m) {
 }
 
 /* One application of the operator T of Eq. (time_shift):
- *   (a, b) at time t0, step h, stencil source (as, bs)  ->  (an, bn) at t0 + h.
+ *   (a, b) at time t0, step h, stencil source (as, bs) at time ts
+ *   ->  (an, bn) at t0 + h.
  * Forward / backward differences Eqs. (a_forward)..(b_backward), combined
  * Crank-Nicolson style, solved in closed form Eqs. (a_t_plus_1), (b_t_plus_1)
  * with readings R2..R5.  The output arrays must not alias the inputs. */
-void apply_T(const oracle_params* p, const Grid& g, double t0, double h,
+void apply_T(const oracle_params* p, const Grid& g, double t0, double h, double ts,
              const double* a, const double* b, const double* as, const double* bs,
              double* an, double* bn) {
     const double nu = 1.0 + h / 2.0;
     const double xi = 1.0 - h / 2.0;
-    double c = p->B * h / (4.0 * g.dphi);
+    double c = B_at(p, (p->flags & ORACLE_MUT_B_STENCIL_START) ? t0 : ts) * h / (4.0 * g.dphi);
     if (p->flags & ORACLE_MUT_ALPHA_STENCIL) c *= p->alpha;
     const double Es = E_at(p, t0);
     const double Ee = (p->flags & ORACLE_MUT_THETA_START_ONLY) ? Es : E_at(p, t0 + h);
+    const double Bs = B_at(p, t0);
+    const double Be = (p->flags & ORACLE_MUT_THETA_START_ONLY) ? Bs : B_at(p, t0 + h);
     const int N = g.N, M = g.M;
 #pragma omp parallel for schedule(static)
     for (int n = 0; n <= N; ++n) {
         const double chi = (n == 1 && !(p->flags & ORACLE_MUT_NO_CHI)) ? 2.0 : 1.0;
         for (int m = 0; m <= M; ++m) {
             const size_t i = (size_t)n * (M + 1) + m;
-            /* mu^t_{n,m} = n beta^t_m dt/2, beta^t_m = E^t + B phi_y(m) */
-            const double th = n * (Es + p->B * g.phi[m]) * h / 2.0;
-            const double th1 = n * (Ee + p->B * g.phi[m]) * h / 2.0;
+            /* mu^t_{n,m} = n beta^t_m dt/2, beta^t_m = E^t + B^t phi_y(m) */
+            const double th = n * (Es + Bs * g.phi[m]) * h / 2.0;
+            const double th1 = n * (Ee + Be * g.phi[m]) * h / 2.0;
             /* the paper's B^t_{n,m} (acts on a) and A^t_{n,m} (acts on b) */
             double Sa;
             if (p->flags & ORACLE_MUT_STENCIL_INDEX)
@@ -333,7 +349,7 @@ int oracle_init(const oracle_params* p, double* aw, double* bw, double* af, doub
     const size_t sz = g.a0.size();
     std::memcpy(aw, g.a0.data(), sz * sizeof(double));
     std::memset(bw, 0, sz * sizeof(double));
-    apply_T(p, g, 0.0, g.dt_eff / 2.0, aw, bw, aw, bw, af, bf);
+    apply_T(p, g, 0.0, g.dt_eff / 2.0, 0.0, aw, bw, aw, bw, af, bf);
     return 0;
 }
 
@@ -354,12 +370,12 @@ int oracle_advance(const oracle_params* p, long long k0, long long nsteps, doubl
         const long long k = k0 + s;
         const double t = k * h;
         /* z^{t+1} = T(z^t; S(z^{t+1/2})) */
-        apply_T(p, g, t, h, aw, bw, af, bf, an.data(), bn.data());
+        apply_T(p, g, t, h, t + 0.5 * h, aw, bw, af, bf, an.data(), bn.data());
         /* z^{t+3/2} = T(z^{t+1/2}; S(z^{t+1})) -- source is the NEW whole grid */
         if (p->flags & ORACLE_MUT_STALE_SOURCE)
-            apply_T(p, g, t + 0.5 * h, h, af, bf, aw, bw, afn.data(), bfn.data());
+            apply_T(p, g, t + 0.5 * h, h, t + h, af, bf, aw, bw, afn.data(), bfn.data());
         else
-            apply_T(p, g, t + 0.5 * h, h, af, bf, an.data(), bn.data(), afn.data(),
+            apply_T(p, g, t + 0.5 * h, h, t + h, af, bf, an.data(), bn.data(), afn.data(),
                     bfn.data());
         std::memcpy(aw, an.data(), sz * sizeof(double));
         std::memcpy(bw, bn.data(), sz * sizeof(double));

@@ -35,7 +35,7 @@ class bte_params(ctypes.Structure):
         ("phiy_min", ctypes.c_double), ("phiy_max", ctypes.c_double), ("dt", ctypes.c_double),
         ("periods", ctypes.c_double), ("t_max", ctypes.c_double), ("avg_window", ctypes.c_double),
         ("n_max", ctypes.c_int32), ("m_points", ctypes.c_int32), ("precision", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("reserved", ctypes.c_int32), ("B_omega", ctypes.c_double), ("B_phase", ctypes.c_double),
     ]
 
 
@@ -140,6 +140,8 @@ def to_params(p) -> bte_params:
     s.m_points = int(g("m_points"))
     s.precision = int(g("precision", FP64))
     s.reserved = 0
+    s.B_omega = float(g("B_omega", 0.0))
+    s.B_phase = float(g("B_phase", 0.0))
     return s
 
 

@@ -54,7 +54,8 @@ struct TimeGrid {
 int validate(const bte_params* p) {
     if (!p) return fail(BTE_EINVAL, "params is NULL");
     const double v[] = {p->E_dc, p->E_omega, p->omega, p->B, p->mu, p->alpha,
-                        p->phiy_min, p->phiy_max, p->dt, p->periods, p->t_max, p->avg_window};
+                        p->phiy_min, p->phiy_max, p->dt, p->periods, p->t_max, p->avg_window,
+                        p->B_omega, p->B_phase};
     for (double x : v)
         if (!std::isfinite(x)) return fail(BTE_EINVAL, "non-finite parameter");
     if (p->n_max < 1) return fail(BTE_EINVAL, "n_max must be >= 1");
@@ -178,7 +179,7 @@ struct Layout {
     int G, H, pitch, tile_m, chunk_n, vec, ts, ntx, nty;
     size_t elem;
     size_t off_state[8];
-    size_t off_row_a0, off_col_g, off_col_bphi, off_ew, off_ef, off_tv, off_tn, off_part,
+    size_t off_row_a0, off_col_g, off_col_phi, off_ew, off_ef, off_tv, off_tn, off_part,
         off_ticket, off_err, off_base, off_fin, total;
 };
 
@@ -214,13 +215,13 @@ int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L
     o += align_up((size_t)N1 * L.elem, 256);
     L.off_col_g = o;
     o += align_up((size_t)L.pitch * L.elem, 256);
-    L.off_col_bphi = o;
+    L.off_col_phi = o;
     o += align_up((size_t)L.pitch * L.elem, 256);
     const long long Pt = tg.P > 0 ? tg.P : 1;
     L.off_ew = o;
-    o += align_up((size_t)(Pt + 2) * 8, 256);
+    o += align_up((size_t)3 * (Pt + 2) * L.elem, 256);
     L.off_ef = o;
-    o += align_up((size_t)(Pt + 2) * 8, 256);
+    o += align_up((size_t)3 * (Pt + 2) * L.elem, 256);
     L.off_tv = o;
     o += align_up((size_t)(tg.K + 1) * 8, 256);
     L.off_tn = o;
@@ -279,9 +280,9 @@ bte::StepArgs<T> step_args(const bte_handle* h) {
     }
     a.row_a0 = h->ptr<T>(L.off_row_a0);
     a.col_g = h->ptr<T>(L.off_col_g);
-    a.col_bphi = h->ptr<T>(L.off_col_bphi);
-    a.e_whole = h->ptr<double>(L.off_ew);
-    a.e_frac = h->ptr<double>(L.off_ef);
+    a.col_phi = h->ptr<T>(L.off_col_phi);
+    a.e_whole = h->ptr<T>(L.off_ew);
+    a.e_frac = h->ptr<T>(L.off_ef);
     a.base = h->ptr<long long>(L.off_base);
     a.trace_v = h->ptr<double>(L.off_tv);
     a.trace_n = h->ptr<double>(L.off_tn);
@@ -292,6 +293,7 @@ bte::StepArgs<T> step_args(const bte_handle* h) {
     a.M = h->p.m_points - 1;
     a.pitch = L.pitch;
     a.P = h->tg.P > 0 ? (int)h->tg.P : 1;
+    a.dstride = a.P + 2;
     a.tile_m = L.tile_m;
     a.chunk_n = L.chunk_n;
     a.ntx = L.ntx;
@@ -303,7 +305,6 @@ bte::StepArgs<T> step_args(const bte_handle* h) {
     a.hh = (T)(0.5 * dt);
     a.nu = (T)(1.0 + 0.5 * dt);
     a.xi = (T)(1.0 - 0.5 * dt);
-    a.c = (T)(h->p.B * dt / (4.0 * h->dphi));
     const double sq = std::sqrt(h->p.alpha);
     a.vscale = kPi * sq * h->dphi;
     a.nscale = 2.0 * kPi * sq * h->dphi;
@@ -311,57 +312,85 @@ bte::StepArgs<T> step_args(const bte_handle* h) {
 }
 
 /* Host tables of one instance (Sec. 2): row factors sigma_n I_n/(pi I_0),
- * column factors sqrt(mu/(2 pi alpha)) exp(-mu phi^2/2) and B phi_m laid out
- * with G ghost columns, and the FP64 drive E(i dt), E((i+1/2) dt) over one
- * period plus two entries (Sec. 2, E(t) = E_dc + E_omega cos(omega t)). */
+ * column factors sqrt(mu/(2 pi alpha)) exp(-mu phi^2/2) and phi_m laid out
+ * with G ghost columns, and the drive (FP64, rounded to T once) over one
+ * period plus two entries
+ * in two [3][P+2] tables: at the whole-grid times i dt (ew) and the
+ * fractional-grid times (i + 1/2) dt (ef), E(t) (Sec. 2, E(t) = E_dc +
+ * E_omega cos(omega t)), B(t) = B + B_omega cos(omega t + B_phase), and the
+ * stencil coefficient B dt/(4 dphi) of the half-step starting at t, with B
+ * taken at the time of the other grid, t + dt/2. */
 template <typename T>
 void build_tables(const bte_params& p, const TimeGrid& tg, int G, int pitch, double dphi,
-                  std::vector<T>& row, std::vector<T>& colg, std::vector<T>& colb,
-                  std::vector<double>& ew, std::vector<double>& ef, double& r1) {
+                  std::vector<T>& row, std::vector<T>& colg, std::vector<T>& colp,
+                  std::vector<T>& ew, std::vector<T>& ef, double& r1) {
     const int N1 = p.n_max + 1, M1 = p.m_points;
     std::vector<double> r(N1);
     miller_ratio(p.mu, p.n_max, r.data());
     r1 = r[1];
     row.assign(N1, (T)0);
     colg.assign(pitch, (T)0);
-    colb.assign(pitch, (T)0);
+    colp.assign(pitch, (T)0);
     for (int n = 0; n < N1; ++n) row[n] = (T)((n == 0 ? 0.5 : 1.0) * r[n] / kPi);
     const double pref = std::sqrt(p.mu / (2.0 * kPi * p.alpha));
     for (int m = 0; m < M1; ++m) {
         const double phi = p.phiy_min + m * dphi;
         colg[G + m] = (T)(pref * std::exp(-0.5 * p.mu * phi * phi));
-        colb[G + m] = (T)(p.B * phi);
+        colp[G + m] = (T)phi;
     }
     const long long Pt = tg.P > 0 ? tg.P : 1;
-    ew.assign(Pt + 2, 0.0);
-    ef.assign(Pt + 2, 0.0);
-    for (long long q = 0; q <= Pt + 1; ++q) {
-        if (tg.P > 0) {
-            ew[q] = p.E_dc + p.E_omega * std::cos(kTwoPi * (double)q / (double)Pt);
-            ef[q] = p.E_dc + p.E_omega * std::cos(kTwoPi * ((double)q + 0.5) / (double)Pt);
-        } else {
-            ew[q] = ef[q] = p.E_dc + p.E_omega;
-        }
+    const long long S = Pt + 2;
+    ew.assign(3 * S, (T)0);
+    ef.assign(3 * S, (T)0);
+    const double dt = tg.dt_eff;
+    /* drive phase of time (q + s/2) dt: 2 pi (q + s/2)/P, or 0 when omega == 0 */
+    auto ph = [&](long long q, int s) {
+        return tg.P > 0 ? kTwoPi * ((double)q + 0.5 * s) / (double)Pt : 0.0;
+    };
+    auto Bt = [&](double x) { return p.B + p.B_omega * std::cos(x + p.B_phase); };
+    for (long long q = 0; q < S; ++q) {
+        ew[q] = (T)(p.E_dc + p.E_omega * std::cos(ph(q, 0)));
+        ef[q] = (T)(p.E_dc + p.E_omega * std::cos(ph(q, 1)));
+        ew[S + q] = (T)Bt(ph(q, 0));
+        ef[S + q] = (T)Bt(ph(q, 1));
+        ew[2 * S + q] = (T)(Bt(ph(q, 1)) * dt / (4.0 * dphi));
+        ef[2 * S + q] = (T)(Bt(ph(q, 2)) * dt / (4.0 * dphi));
     }
+}
+
+/* Start-up half step (Sec. 3, reading R6): T with dt/2 from t = 0, the
+ * initial state as its own stencil source, so the stencil coefficient takes
+ * B(0); the rotation takes E and B at 0 and dt/2. */
+template <typename T>
+void startup_drive(const bte_params& p, double dt_eff, double dphi, bte::ApplyArgs<T>& a) {
+    const double hs = 0.5 * dt_eff;
+    a.E_start = p.E_dc + p.E_omega;
+    a.E_end = p.E_dc + p.E_omega * std::cos(p.omega * hs);
+    a.B_start = p.B + p.B_omega * std::cos(p.B_phase);
+    a.B_end = p.B + p.B_omega * std::cos(p.omega * hs + p.B_phase);
+    a.h = (T)hs;
+    a.hh = (T)(0.5 * hs);
+    a.nu = (T)(1.0 + 0.5 * hs);
+    a.xi = (T)(1.0 - 0.5 * hs);
+    a.c = (T)(a.B_start * hs / (4.0 * dphi));
 }
 
 template <typename T>
 int upload_tables(bte_handle* h) {
     const Layout& L = h->L;
     const int N1 = h->p.n_max + 1;
-    std::vector<T> row, colg, colb;
-    std::vector<double> ew, ef;
-    build_tables<T>(h->p, h->tg, L.G, L.pitch, h->dphi, row, colg, colb, ew, ef, h->r1);
+    std::vector<T> row, colg, colp, ew, ef;
+    build_tables<T>(h->p, h->tg, L.G, L.pitch, h->dphi, row, colg, colp, ew, ef, h->r1);
     const long long Pt = h->tg.P > 0 ? h->tg.P : 1;
     CU(cudaMemcpyAsync(h->ptr<T>(L.off_row_a0), row.data(), N1 * sizeof(T), cudaMemcpyHostToDevice,
                        h->stream));
     CU(cudaMemcpyAsync(h->ptr<T>(L.off_col_g), colg.data(), L.pitch * sizeof(T),
                        cudaMemcpyHostToDevice, h->stream));
-    CU(cudaMemcpyAsync(h->ptr<T>(L.off_col_bphi), colb.data(), L.pitch * sizeof(T),
+    CU(cudaMemcpyAsync(h->ptr<T>(L.off_col_phi), colp.data(), L.pitch * sizeof(T),
                        cudaMemcpyHostToDevice, h->stream));
-    CU(cudaMemcpyAsync(h->ptr<double>(L.off_ew), ew.data(), (Pt + 2) * 8, cudaMemcpyHostToDevice,
+    CU(cudaMemcpyAsync(h->ptr<T>(L.off_ew), ew.data(), 3 * (Pt + 2) * sizeof(T), cudaMemcpyHostToDevice,
                        h->stream));
-    CU(cudaMemcpyAsync(h->ptr<double>(L.off_ef), ef.data(), (Pt + 2) * 8, cudaMemcpyHostToDevice,
+    CU(cudaMemcpyAsync(h->ptr<T>(L.off_ef), ef.data(), 3 * (Pt + 2) * sizeof(T), cudaMemcpyHostToDevice,
                        h->stream));
     CU(cudaStreamSynchronize(h->stream)); /* host vectors go out of scope */
     return BTE_OK;
@@ -395,18 +424,11 @@ int initialise(bte_handle* h, bool full, bool sync) {
     a.bn = h->ptr<T>(L.off_state[3]);
     a.row_a0 = h->ptr<T>(L.off_row_a0);
     a.col_g = h->ptr<T>(L.off_col_g);
-    a.col_bphi = h->ptr<T>(L.off_col_bphi);
+    a.col_phi = h->ptr<T>(L.off_col_phi);
     a.N = p.n_max;
     a.M = p.m_points - 1;
     a.pitch = L.pitch;
-    const double hs = 0.5 * h->tg.dt_eff;
-    a.E_start = p.E_dc + p.E_omega;
-    a.E_end = p.E_dc + p.E_omega * std::cos(p.omega * hs);
-    a.h = (T)hs;
-    a.hh = (T)(0.5 * hs);
-    a.nu = (T)(1.0 + 0.5 * hs);
-    a.xi = (T)(1.0 - 0.5 * hs);
-    a.c = (T)(p.B * hs / (4.0 * h->dphi));
+    startup_drive<T>(p, h->tg.dt_eff, h->dphi, a);
     rc = bte::launch_apply<T>(a, h->stream);
     if (rc) return fail(BTE_ECUDA, "start-up kernel: %s", cudaGetErrorString((cudaError_t)rc));
     const bte::StepArgs<T> sa = step_args<T>(h);
@@ -529,7 +551,7 @@ struct BatchPoint {
     int N1, M1, ntx, nty, pitch, items;
     double dphi;
     size_t state_off, state_bytes, tab_off; /* within the batch workspace */
-    size_t o_row, o_colg, o_colb, o_ew, o_ef, o_part, o_ticket, o_acc; /* within the tables */
+    size_t o_row, o_colg, o_colp, o_ew, o_ef, o_part, o_ticket, o_acc; /* within the tables */
     size_t tab_bytes;
     double r1;
 };
@@ -567,12 +589,12 @@ int run_batch(const bte_params* p, std::vector<BatchPoint>& pts, size_t first, s
         t += align_up((size_t)b.N1 * elem, 256);
         b.o_colg = t;
         t += align_up((size_t)b.pitch * elem, 256);
-        b.o_colb = t;
+        b.o_colp = t;
         t += align_up((size_t)b.pitch * elem, 256);
         b.o_ew = t;
-        t += align_up((size_t)(Pt + 2) * 8, 256);
+        t += align_up((size_t)3 * (Pt + 2) * elem, 256);
         b.o_ef = t;
-        t += align_up((size_t)(Pt + 2) * 8, 256);
+        t += align_up((size_t)3 * (Pt + 2) * elem, 256);
         b.o_part = t;
         t += align_up((size_t)2 * b.ntx * 8, 256);
         b.o_ticket = t;
@@ -617,15 +639,14 @@ int run_batch(const bte_params* p, std::vector<BatchPoint>& pts, size_t first, s
     for (size_t i = first; i < last; ++i) {
         BatchPoint& b = pts[i];
         const bte_params& pp = p[b.idx];
-        std::vector<T> row, colg, colb;
-        std::vector<double> ew, ef;
-        build_tables<T>(pp, b.tg, G, b.pitch, b.dphi, row, colg, colb, ew, ef, b.r1);
+        std::vector<T> row, colg, colp, ew, ef;
+        build_tables<T>(pp, b.tg, G, b.pitch, b.dphi, row, colg, colp, ew, ef, b.r1);
         unsigned char* hb = host.data() + (b.tab_off - tables_begin);
         std::memcpy(hb + b.o_row, row.data(), row.size() * elem);
         std::memcpy(hb + b.o_colg, colg.data(), colg.size() * elem);
-        std::memcpy(hb + b.o_colb, colb.data(), colb.size() * elem);
-        std::memcpy(hb + b.o_ew, ew.data(), ew.size() * 8);
-        std::memcpy(hb + b.o_ef, ef.data(), ef.size() * 8);
+        std::memcpy(hb + b.o_colp, colp.data(), colp.size() * elem);
+        std::memcpy(hb + b.o_ew, ew.data(), ew.size() * elem);
+        std::memcpy(hb + b.o_ef, ef.data(), ef.size() * elem);
         unsigned char* tb = mem + b.tab_off;
         bte::BatchInst<T>& R = rec[i - first];
         for (int s = 0; s < 2; ++s) {
@@ -637,9 +658,9 @@ int run_batch(const bte_params* p, std::vector<BatchPoint>& pts, size_t first, s
         }
         R.row_a0 = reinterpret_cast<const T*>(tb + b.o_row);
         R.col_g = reinterpret_cast<const T*>(tb + b.o_colg);
-        R.col_bphi = reinterpret_cast<const T*>(tb + b.o_colb);
-        R.e_whole = reinterpret_cast<const double*>(tb + b.o_ew);
-        R.e_frac = reinterpret_cast<const double*>(tb + b.o_ef);
+        R.col_phi = reinterpret_cast<const T*>(tb + b.o_colp);
+        R.e_whole = reinterpret_cast<const T*>(tb + b.o_ew);
+        R.e_frac = reinterpret_cast<const T*>(tb + b.o_ef);
         R.part = reinterpret_cast<double*>(tb + b.o_part);
         R.ticket = reinterpret_cast<unsigned*>(tb + b.o_ticket);
         R.acc = reinterpret_cast<double*>(tb + b.o_acc);
@@ -649,6 +670,7 @@ int run_batch(const bte_params* p, std::vector<BatchPoint>& pts, size_t first, s
         R.M = b.M1 - 1;
         R.pitch = b.pitch;
         R.P = b.tg.P > 0 ? (int)b.tg.P : 1;
+        R.dstride = R.P + 2;
         R.ntx = b.ntx;
         R.nty = b.nty;
         R.item0 = item0;
@@ -659,7 +681,6 @@ int run_batch(const bte_params* p, std::vector<BatchPoint>& pts, size_t first, s
         R.hh = (T)(0.5 * dt);
         R.nu = (T)(1.0 + 0.5 * dt);
         R.xi = (T)(1.0 - 0.5 * dt);
-        R.c = (T)(pp.B * dt / (4.0 * b.dphi));
         const double sq = std::sqrt(pp.alpha);
         R.vscale = kPi * sq * b.dphi;
         R.nscale = 2.0 * kPi * sq * b.dphi;
@@ -699,18 +720,11 @@ int run_batch(const bte_params* p, std::vector<BatchPoint>& pts, size_t first, s
         a.bn = R.b_f[0];
         a.row_a0 = R.row_a0;
         a.col_g = R.col_g;
-        a.col_bphi = R.col_bphi;
+        a.col_phi = R.col_phi;
         a.N = R.N;
         a.M = R.M;
         a.pitch = R.pitch;
-        const double hs = 0.5 * b.tg.dt_eff;
-        a.E_start = pp.E_dc + pp.E_omega;
-        a.E_end = pp.E_dc + pp.E_omega * std::cos(pp.omega * hs);
-        a.h = (T)hs;
-        a.hh = (T)(0.5 * hs);
-        a.nu = (T)(1.0 + 0.5 * hs);
-        a.xi = (T)(1.0 - 0.5 * hs);
-        a.c = (T)(pp.B * hs / (4.0 * b.dphi));
+        startup_drive<T>(pp, b.tg.dt_eff, b.dphi, a);
         if (!r) r = bte::launch_apply<T>(a, st);
         if (!r)
             r = bte::launch_observe<T>(R.a_w[0], R.b_w[0], R.M, R.pitch, R.vscale, R.nscale,

@@ -39,9 +39,14 @@ struct StepArgs {
     T* b_f[2];
     const T* row_a0;      /* [N+1]   sigma_n I_n/I_0 / pi                        */
     const T* col_g;       /* [pitch] sqrt(mu/(2 pi alpha)) exp(-mu phi^2/2), 0 in ghosts */
-    const T* col_bphi;    /* [pitch] B phi_y(m), 0 in ghosts                    */
-    const double* e_whole;/* [P+2]   E(i dt_eff)                                 */
-    const double* e_frac; /* [P+2]   E((i + 1/2) dt_eff)                         */
+    const T* col_phi;     /* [pitch] phi_y(m), 0 in ghosts                      */
+    const T* e_whole;     /* [3][dstride] at t = i dt_eff: E(t), B(t), and the
+                             stencil coefficient B(t + dt/2) dt/(4 dphi) of the
+                             whole-grid half-step from t (i = 0..P+1); FP64
+                             values rounded to T once on the host             */
+    const T* e_frac;      /* [3][dstride] at t = (i + 1/2) dt_eff: E(t), B(t),
+                             and B(t + dt/2) dt/(4 dphi) of the fractional
+                             half-step from t                                   */
     const long long* base;/* device step counter: the launch advances step base+i */
     double* trace_v;      /* [K+1] whole-grid v_dr samples                       */
     double* trace_n;      /* [K+1] whole-grid norm samples                       */
@@ -49,10 +54,11 @@ struct StepArgs {
     unsigned* ticket;     /* arrival counter of the row-0 CTAs                   */
     int* err;             /* device error word (timeouts)                        */
     int N, M, pitch, P;
+    int dstride;          /* row stride of the drive tables (>= P + 2)          */
     int tile_m, chunk_n, ntx, nty;
     int vec;              /* phi_y columns per compute thread (2 or 4)         */
     int grid;             /* persistent CTAs; items are ntx * nty              */
-    T h, hh, nu, xi, c;   /* dt, dt/2, 1 + dt/2, 1 - dt/2, B dt/(4 dphi)         */
+    T h, hh, nu, xi;      /* dt, dt/2, 1 + dt/2, 1 - dt/2                        */
     double vscale, nscale;/* pi sqrt(alpha) dphi, 2 pi sqrt(alpha) dphi          */
 };
 
@@ -68,9 +74,9 @@ struct BatchInst {
     T* b_f[2];
     const T* row_a0;
     const T* col_g;
-    const T* col_bphi;
-    const double* e_whole;
-    const double* e_frac;
+    const T* col_phi;
+    const T* e_whole;     /* drive tables as in StepArgs                         */
+    const T* e_frac;
     double* part;         /* [2][ntx] per-tile partial sums                      */
     unsigned* ticket;     /* arrival counter of the row-0 items                  */
     double* acc;          /* [8]: sum v cos(omega t) and sum v over the window,
@@ -78,8 +84,9 @@ struct BatchInst {
                              latest step, v and norm of step 0               */
     long long K, Kw;      /* steps of the run, window samples                    */
     int N, M, pitch, P, ntx, nty;
+    int dstride;
     int item0;            /* index of the instance's first work item            */
-    T h, hh, nu, xi, c;
+    T h, hh, nu, xi;
     double vscale, nscale;
     double omega, dt_eff;
 };
@@ -115,10 +122,10 @@ struct ApplyArgs {
     const T* a;  const T* b;     /* state at t0                                */
     const T* as; const T* bs;    /* stencil source                             */
     T* an; T* bn;                /* output (may not alias the inputs)          */
-    const T* row_a0; const T* col_g; const T* col_bphi;
+    const T* row_a0; const T* col_g; const T* col_phi;
     int N, M, pitch;
-    double E_start, E_end;
-    T h, hh, nu, xi, c;
+    double E_start, E_end, B_start, B_end;
+    T h, hh, nu, xi, c;   /* c: stencil coefficient at the source's time        */
 };
 
 struct FinalArgs {

@@ -46,9 +46,9 @@ __global__ void apply_kernel(ApplyArgs<T> A) {
     if (m > A.M || n > A.N) return;
     const int c = G + m;
     const T chi = (n == 1) ? (T)2 : (T)1;
-    const T bp = A.col_bphi[c];
-    const T th = (T)n * (((T)A.E_start + bp) * A.hh);
-    const T th1 = (T)n * (((T)A.E_end + bp) * A.hh);
+    const T ph = A.col_phi[c];
+    const T th = (T)n * (((T)A.E_start + (T)A.B_start * ph) * A.hh);
+    const T th1 = (T)n * (((T)A.E_end + (T)A.B_end * ph) * A.hh);
     const int N = A.N, P = A.pitch;
     const T bu = ld_or0(A.bs, n + 1, c + 1, N, P) - ld_or0(A.bs, n + 1, c - 1, N, P);
     const T bd = (n - 1 >= 1) ? ld_or0(A.bs, n - 1, c + 1, N, P) - ld_or0(A.bs, n - 1, c - 1, N, P)

@@ -95,6 +95,24 @@ __device__ __forceinline__ void diff_ld(const T* p, T (&d)[RV<T>::V]) {
     d[V - 1] = right - own[V - 2];
 }
 
+/* Drive of one half-step: E and B at its start (E0, B0) and end (E1, B1),
+ * and its stencil coefficient, read from a [3][stride] drive table (E, B,
+ * coefficient; FP64 values rounded to T once on the host) at row kk. */
+template <typename T>
+struct Half {
+    T E0, E1, B0, B1, cc;
+};
+template <typename T>
+__device__ __forceinline__ Half<T> half_drive(const T* tab, int stride, int kk) {
+    Half<T> d;
+    d.E0 = tab[kk];
+    d.E1 = tab[kk + 1];
+    d.B0 = tab[stride + kk];
+    d.B1 = tab[stride + kk + 1];
+    d.cc = tab[2 * stride + kk];
+    return d;
+}
+
 /* One half-step (Sec. 3, Eqs. a_t_plus_1, b_t_plus_1, in increment form) on
  * the V cells of a group at harmonic n, in place: oA, oB the own grid's a, b;
  * da_u, da_d, db_u, db_d the phi_y differences of the other grid's a and b
@@ -174,7 +192,7 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
         const int r0 = min(N1, rank * rows_per), r1 = min(N1, r0 + rows_per), R = r1 - r0;
         const int ncg = (M + 1 + V - 1) / V;
         const long long K = I.K, Kw = I.Kw;
-        const T h = I.h, hh = I.hh, nu = I.nu, xi = I.xi, cc = I.c;
+        const T h = I.h, hh = I.hh, nu = I.nu, xi = I.xi;
         /* shared-memory layout of this point: 4 arrays of rows_per + 2 rows
          * (halo, own rows, halo) with row stride P = ghost + columns + ghost */
         const int P = LG + ncg * V + V;
@@ -184,8 +202,8 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
         T* sAf = sBw + arr;
         T* sBf = sAf + arr;
         T* sG = sBf + arr; /* [P] column factor of a0 */
-        T* sBp = sG + P;   /* [P] B phi_m */
-        T* sR = sBp + P;   /* [rows_per + 2] row factor of a0, rows r0-1 .. r0+rows_per */
+        T* sPh = sG + P;   /* [P] phi_m */
+        T* sR = sPh + P;   /* [rows_per + 2] row factor of a0, rows r0-1 .. r0+rows_per */
 
         /* ---- load: zero everything, then rows r0-1 .. r1 that exist ---- */
         for (size_t q = tid; q < 4 * arr + 2 * (size_t)P + rows_per + 2; q += nthr) sAw[q] = (T)0;
@@ -204,7 +222,7 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
             }
             for (int q = tid; q < ncg * V; q += nthr) {
                 sG[LG + q] = I.col_g[GG + q];
-                sBp[LG + q] = I.col_bphi[GG + q];
+                sPh[LG + q] = I.col_phi[GG + q];
             }
             for (int q = tid; q < R + 2; q += nthr) {
                 const int n = r0 - 1 + q;
@@ -250,7 +268,7 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
 
         /* one half-step on the rows of this CTA: own grid (o) updated in place
          * from the other grid (x) */
-        auto half_interior = [&](int o, int x, const T (&E0)[V], const T (&E1)[V]) {
+        auto half_interior = [&](int o, int x, const Half<T>& D) {
             for (int pass = 0; pass < npass; ++pass) {
                 const int g = pass * cpp + gl;
                 const bool g_on = t_on && g < ncg;
@@ -260,10 +278,10 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                 T gc[V], t0[V], t1[V];
 #pragma unroll
                 for (int e = 0; e < V; ++e) {
-                    const T bp = sBp[LG + m0 + e];
+                    const T ph = sPh[LG + m0 + e];
                     gc[e] = sG[LG + m0 + e];
-                    t0[e] = (E0[0] + bp) * hh;
-                    t1[e] = (E1[0] + bp) * hh;
+                    t0[e] = (D.E0 + D.B0 * ph) * hh;
+                    t1[e] = (D.E1 + D.B1 * ph) * hh;
                 }
                 const T* xa = sAw + x * arr + LG + m0; /* other grid, shared row 0 */
                 for (int ch = 0; ch < 2; ++ch) {
@@ -288,7 +306,7 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                         const size_t c = (size_t)(il + 1) * P + LG + m0;
                         cell_group<T>(sAw + o * arr + c, sAw + (o + 1) * arr + c, da_u, da_d, db_u,
                                       db_d, r0 + il, m0, M, h * sR[il + 1], gc, t0, t1, nu, xi, h,
-                                      cc, on);
+                                      D.cc, on);
 #pragma unroll
                         for (int e = 0; e < V; ++e) {
                             da_u[e] = da_d[e];
@@ -298,7 +316,7 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                 }
             }
         };
-        auto half_boundary = [&](int o, int x, const T (&E0)[V], const T (&E1)[V]) {
+        auto half_boundary = [&](int o, int x, const Half<T>& D) {
             for (int u = tid; u < nbnd * ncg; u += nthr) {
                 const int b = u / ncg, g = u - b * ncg;
                 const int il = b == 0 ? 0 : R - 1;
@@ -316,13 +334,13 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                 T gc[V], t0[V], t1[V];
 #pragma unroll
                 for (int e = 0; e < V; ++e) {
-                    const T bp = sBp[LG + m0 + e];
+                    const T ph = sPh[LG + m0 + e];
                     gc[e] = sG[LG + m0 + e];
-                    t0[e] = (E0[0] + bp) * hh;
-                    t1[e] = (E1[0] + bp) * hh;
+                    t0[e] = (D.E0 + D.B0 * ph) * hh;
+                    t1[e] = (D.E1 + D.B1 * ph) * hh;
                 }
                 cell_group<T>(sAw + o * arr + c, sAw + (o + 1) * arr + c, da_u, da_d, db_u, db_d,
-                              r0 + il, m0, M, h * sR[il + 1], gc, t0, t1, nu, xi, h, cc, true);
+                              r0 + il, m0, M, h * sR[il + 1], gc, t0, t1, nu, xi, h, D.cc, true);
             }
         };
 
@@ -336,15 +354,12 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
         cluster_arrive(); /* initial state loaded */
         for (long long k = 0; k < K; ++k) {
             const int kk = PP > 0 ? (int)(k % PP) : 0;
-            T Ew0[V], Ew1[V], Ef0[V], Ef1[V];
-            Ew0[0] = (T)I.e_whole[kk];
-            Ew1[0] = (T)I.e_whole[kk + 1];
-            Ef0[0] = (T)I.e_frac[kk];
-            Ef1[0] = (T)I.e_frac[kk + 1];
+            const Half<T> Dw = half_drive<T>(I.e_whole, I.dstride, kk);
+            const Half<T> Df = half_drive<T>(I.e_frac, I.dstride, kk);
             /* ---- whole grid: z_w^{k+1} = T(z_w^k; S(z_f^{k+1/2})) ---- */
-            half_interior(0, 2, Ew0, Ew1);
+            half_interior(0, 2, Dw);
             cluster_wait();
-            half_boundary(0, 2, Ew0, Ew1);
+            half_boundary(0, 2, Dw);
             __syncthreads();
             cluster_arrive();
             if (rank == 0) {
@@ -369,9 +384,9 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                 }
             }
             /* ---- fractional grid: z_f^{k+3/2} = T(z_f^{k+1/2}; S(z_w^{k+1})) ---- */
-            half_interior(2, 0, Ef0, Ef1);
+            half_interior(2, 0, Df);
             cluster_wait();
-            half_boundary(2, 0, Ef0, Ef1);
+            half_boundary(2, 0, Df);
             __syncthreads();
             cluster_arrive();
             if (rank == 0 && tid == 0) {

@@ -8,7 +8,7 @@
  * 4-point diagonal stencil of the paper's A^t / B^t terms, which only needs
  * the central differences  D x_r(m) = x_r(m+1) - x_r(m-1)  of rows r = n+-1:
  *     B^t_{n,m} = c (D b_{n+1} - D b_{n-1}),  A^t_{n,m} = c (chi(n) D a_{n-1} - D a_{n+1}),
- *     c = B dt / (4 dphi).
+ *     c = B(t_s) dt / (4 dphi), t_s the time of the grid that supplies S.
  *
  * Work items.  A grid is cut into items of tile_m phi_y columns x chunk_n
  * harmonic rows.  Persistent CTAs take items q = blockIdx.x, +gridDim.x, ...
@@ -162,14 +162,35 @@ struct View {
     const T *gFa, *gFb, *gWa, *gWb; /* old state (set cur)          */
     T *oWa, *oFa;                    /* new state (set nxt)          */
     size_t dWb, dFb;                 /* b array offset from a array  */
-    const T *row_a0, *col_g, *col_bphi;
+    const T *row_a0, *col_g, *col_phi;
     double *part;
     unsigned* ticket;
     int N, M, pitch, ntx, inst, q0; /* q0: the instance's first item */
     long long k;
     bool active;                     /* instance still running       */
-    T Ews, Ewe, Efs, Efe, h, hh, nu, xi, cc;
+    T Ews, Ewe, Efs, Efe; /* E at the start / end of the whole and fractional half-steps */
+    T Bws, Bwe, Bfs, Bfe; /* B at the same times                                         */
+    T ccw, ccf;           /* stencil coefficients of the two half-steps                   */
+    T h, hh, nu, xi;
 };
+
+/* Drive of the half-steps of step k (kk = k mod P): E and B at the start and
+ * end of each half-step and the two stencil coefficients, from the
+ * [3][stride] tables (FP64 values rounded to T once on the host, so no
+ * conversion here). */
+template <typename T>
+__device__ __forceinline__ void drive(View<T>& v, const T* ew, const T* ef, int stride, int kk) {
+    v.Ews = ew[kk];
+    v.Ewe = ew[kk + 1];
+    v.Efs = ef[kk];
+    v.Efe = ef[kk + 1];
+    v.Bws = ew[stride + kk];
+    v.Bwe = ew[stride + kk + 1];
+    v.Bfs = ef[stride + kk];
+    v.Bfe = ef[stride + kk + 1];
+    v.ccw = ew[2 * stride + kk];
+    v.ccf = ef[2 * stride + kk];
+}
 
 /* Instance of item q: single-instance launches use A; batched ones look the
  * instance up in the item -> instance table. */
@@ -188,7 +209,7 @@ __device__ __forceinline__ void make_view(View<T>& v, int q, const StepArgs<T>& 
         v.dFb = (size_t)(A.b_f[cur ^ 1] - v.oFa);
         v.row_a0 = A.row_a0;
         v.col_g = A.col_g;
-        v.col_bphi = A.col_bphi;
+        v.col_phi = A.col_phi;
         v.part = A.part;
         v.ticket = A.ticket;
         v.N = A.N;
@@ -201,15 +222,11 @@ __device__ __forceinline__ void make_view(View<T>& v, int q, const StepArgs<T>& 
         v.active = true;
         if (with_drive) {
             const int kk = A.P > 0 ? (int)(kbase % A.P) : 0;
-            v.Ews = (T)A.e_whole[kk];
-            v.Ewe = (T)A.e_whole[kk + 1];
-            v.Efs = (T)A.e_frac[kk];
-            v.Efe = (T)A.e_frac[kk + 1];
+            drive<T>(v, A.e_whole, A.e_frac, A.dstride, kk);
             v.h = A.h;
             v.hh = A.hh;
             v.nu = A.nu;
             v.xi = A.xi;
-            v.cc = A.c;
         }
     } else {
         const int lo = __ldg(Bt.item_inst + q);
@@ -226,7 +243,7 @@ __device__ __forceinline__ void make_view(View<T>& v, int q, const StepArgs<T>& 
         v.dFb = (size_t)(I.b_f[cur ^ 1] - v.oFa);
         v.row_a0 = I.row_a0;
         v.col_g = I.col_g;
-        v.col_bphi = I.col_bphi;
+        v.col_phi = I.col_phi;
         v.part = I.part;
         v.ticket = I.ticket;
         v.N = I.N;
@@ -237,15 +254,11 @@ __device__ __forceinline__ void make_view(View<T>& v, int q, const StepArgs<T>& 
         v.active = kbase < I.K;
         if (with_drive && v.active) {
             const int kk = I.P > 0 ? (int)(kbase % I.P) : 0;
-            v.Ews = (T)I.e_whole[kk];
-            v.Ewe = (T)I.e_whole[kk + 1];
-            v.Efs = (T)I.e_frac[kk];
-            v.Efe = (T)I.e_frac[kk + 1];
+            drive<T>(v, I.e_whole, I.e_frac, I.dstride, kk);
             v.h = I.h;
             v.hh = I.hh;
             v.nu = I.nu;
             v.xi = I.xi;
-            v.cc = I.c;
         }
     }
 }
@@ -374,7 +387,7 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
         const int n1 = min(n0 + chunk, N + 1);
         const int S = n1 - n0 + 4;
         const int p0 = G + tx * Wt; /* physical column of the tile's first column */
-        const T h = I.h, hh = I.hh, nu = I.nu, xi = I.xi, cc = I.cc;
+        const T h = I.h, hh = I.hh, nu = I.nu, xi = I.xi, ccw = I.ccw, ccf = I.ccf;
 
         __syncthreads(); /* the previous item is done with sR and sN */
         for (int r = tid; r < n1 - n0 + 2; r += blockDim.x) {
@@ -391,12 +404,12 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
 #pragma unroll
         for (int e = 0; e < V; ++e) {
             ok[e] = is_comp && (c + e - G) <= M;
-            const T bp = ok[e] ? I.col_bphi[c + e] : (T)0;
+            const T ph = ok[e] ? I.col_phi[c + e] : (T)0;
             g[e] = ok[e] ? I.col_g[c + e] : (T)0;
-            ws[e] = (I.Ews + bp) * hh;
-            we[e] = (I.Ewe + bp) * hh;
-            fs[e] = (I.Efs + bp) * hh;
-            fe[e] = (I.Efe + bp) * hh;
+            ws[e] = (I.Ews + I.Bws * ph) * hh;
+            we[e] = (I.Ewe + I.Bwe * ph) * hh;
+            fs[e] = (I.Efs + I.Bfs * ph) * hh;
+            fe[e] = (I.Efe + I.Bfe * ph) * hh;
         }
         const bool all_ok = ok[V - 1];
 
@@ -408,9 +421,9 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
         T hg = 0, hbs = 0, hbe = 0;
         if (hok) {
             hg = I.col_g[hcol];
-            const T bp = I.col_bphi[hcol];
-            hbs = (I.Ews + bp) * hh;
-            hbe = (I.Ewe + bp) * hh;
+            const T ph = I.col_phi[hcol];
+            hbs = (I.Ews + I.Bws * ph) * hh;
+            hbe = (I.Ewe + I.Bwe * ph) * hh;
         }
         __syncthreads(); /* sR ready */
 
@@ -466,8 +479,8 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
 #pragma unroll
                         for (int e = 0; e < V; ++e) {
                             T an, bn;
-                            cn_cell<T>(oa[e], ob[e], cc * (dfb_p1[e] - dfb_m1[e]),
-                                       cc * (chi * dfa_m1[e] - dfa_p1[e]), ha0 * g[e], nf * ws[e],
+                            cn_cell<T>(oa[e], ob[e], ccw * (dfb_p1[e] - dfb_m1[e]),
+                                       ccw * (chi * dfa_m1[e] - dfa_p1[e]), ha0 * g[e], nf * ws[e],
                                        nf * we[e], nu, xi, h, an, bn);
                             wa_n[e] = ok[e] ? an : (T)0;
                             wb_n[e] = (ok[e] && j > 0) ? bn : (T)0;
@@ -504,7 +517,7 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
                             const T Dbd = dn ? fd[LW + hlc + 1] - fd[LW + hlc - 1] : (T)0;
                             const T Dau = up ? ra[hlc + 1] - ra[hlc - 1] : (T)0;
                             const T Dbu = up ? ra[LW + hlc + 1] - ra[LW + hlc - 1] : (T)0;
-                            cn_cell<T>(wa[hlc], wa[LW + hlc], cc * (Dbu - Dbd), cc * (chi * Dad - Dau),
+                            cn_cell<T>(wa[hlc], wa[LW + hlc], ccw * (Dbu - Dbd), ccw * (chi * Dad - Dau),
                                        ha0 * hg, nf * hbs, nf * hbe, nu, xi, h, an, bn);
                             if (j == 0) bn = (T)0;
                         }
@@ -542,8 +555,8 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
                     T fa_n[V], fb_n[V];
 #pragma unroll
                     for (int e = 0; e < V; ++e) {
-                        cn_cell<T>(fa_m1[e], fb_m1[e], cc * (dwb_0[e] - dwb_m2[e]),
-                                   cc * (chi * dwa_m2[e] - dwa_0[e]), ha0 * g[e], nf * fs[e],
+                        cn_cell<T>(fa_m1[e], fb_m1[e], ccf * (dwb_0[e] - dwb_m2[e]),
+                                   ccf * (chi * dwa_m2[e] - dwa_0[e]), ha0 * g[e], nf * fs[e],
                                    nf * fe[e], nu, xi, h, fa_n[e], fb_n[e]);
                         if (r == 0) fb_n[e] = (T)0;
                     }

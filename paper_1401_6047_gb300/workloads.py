@@ -39,6 +39,9 @@ class Params:
     t_max: float = 0.0
     avg_window: float = 10.0
     precision: int = FP64
+    # B(t) = B + B_omega cos(omega t + B_phase); 0 for the paper's constant field
+    B_omega: float = 0.0
+    B_phase: float = 0.0
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)

@@ -114,11 +114,14 @@ def f0_fourier(mu: float, alpha: float, nmax: int, phiy: np.ndarray, nx: int = 1
 
 def characteristics_ac(E_dc: float, E_omega: float, omega: float, B: float, mu: float,
                        nphase: int = 12, nx: int = 64, ny: int = 96, ds: float = 0.01,
-                       smax: float = 25.0, ysig: float = 7.0):
+                       smax: float = 25.0, ysig: float = 7.0, B_omega: float = 0.0,
+                       B_phase: float = 0.0):
     """Periodic-state absorption and time-averaged drift velocity for the
-    drive E(t) = E_dc + E_omega cos(omega t) and constant B, by the method of
-    characteristics (the exact solution of the relaxation-time equation for
-    the divergence-free streaming field (E(t) + B phi_y, -B sin phi_x)):
+    drive E(t) = E_dc + E_omega cos(omega t) and the field
+    B(t) = B + B_omega cos(omega t + B_phase) (constant for B_omega = 0), by
+    the method of characteristics (the exact solution of the relaxation-time
+    equation for the streaming field (E(t) + B(t) phi_y, -B(t) sin phi_x),
+    divergence free at every t):
         v(t) = int_0^inf e^{-u} < sin Phi_x(t; t - u, phi0) >_{f0} du.
     With tau = t - u and the period T = 2 pi/omega, the time averages become
     averages over start phases tau in [0, T):
@@ -143,7 +146,8 @@ def characteristics_ac(E_dc: float, E_omega: float, omega: float, B: float, mu: 
     t0 = tau[:, None, None]
 
     def f(px, py, u):
-        return E_dc + E_omega * np.cos(omega * (t0 + u)) + B * py, -B * np.sin(px)
+        Bt = B + B_omega * np.cos(omega * (t0 + u) + B_phase)
+        return E_dc + E_omega * np.cos(omega * (t0 + u)) + Bt * py, -Bt * np.sin(px)
 
     ns = int(round(smax / ds))
     ns += ns % 2

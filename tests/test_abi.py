@@ -62,7 +62,8 @@ def test_time_grid_closed_form():
 
 @pytest.mark.parametrize("bad", [dict(n_max=0), dict(m_points=2), dict(dt=0.0), dict(mu=0.0),
                                  dict(alpha=-1.0), dict(omega=-2.0), dict(E_dc=float("inf")),
-                                 dict(phiy_max=-20.0), dict(avg_window=25.0), dict(precision=7)])
+                                 dict(phiy_max=-20.0), dict(avg_window=25.0), dict(precision=7),
+                                 dict(B_omega=float("nan")), dict(B_phase=float("inf"))])
 def test_invalid_parameters_rejected_on_host(bad):
     """Validation happens before any CUDA call, so it needs no GPU."""
     with pytest.raises(bte.BteError) as e:

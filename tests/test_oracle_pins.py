@@ -349,6 +349,69 @@ def test_characteristics_ac_at_finite_B():
     assert pin_characteristics_ac() <= 1
 
 
+# --- a time-dependent field B(t) = B + B_omega cos(omega t + B_phase) ----------
+# (reading R13: B sampled where E is, and at the source grid's time in the
+# stencil coefficient)
+
+_BT = dict(B_omega=0.6, B_phase=0.7)
+
+
+def pin_order_dt_bt(flags=0):
+    """With B(t) the scheme stays second order in dt; sampling B at the
+    wrong time (the rotation's end value, or the stencil coefficient at the
+    start of the half-step) leaves a first-order error (planted mistakes
+    below give orders 1.0-1.05)."""
+    rs = [oracle.solve(_conv_params(dt=d, **_BT), flags) for d in (1e-2, 5e-3, 2.5e-3)]
+    oA = _order(*(r.A for r in rs))
+    ov = _order(*(r.v_dc for r in rs))
+    return max(abs(oA - 2.0), abs(ov - 2.0)) / 0.2
+
+
+def test_second_order_in_dt_with_time_dependent_B():
+    assert pin_order_dt_bt() <= 1
+
+
+def pin_characteristics_bt(flags=0):
+    """B(t) and a time-dependent drive: absorption and time-averaged drift
+    from the oracle, Richardson-extrapolated in dphi, equal the
+    characteristics integral with B(t) (tests/analytic.py; the streaming
+    field stays divergence free at every t).  The integral's own error at
+    the resolution used is about 1e-4 relative on the small absorption
+    (0.029: doubling the start phases moves it by 1.1e-4) and below 1e-6 on
+    the drift (0.383), hence the two tolerances."""
+    if "bt" not in _CHAR_CACHE:
+        _CHAR_CACHE["bt"] = an.characteristics_ac(1.0, 0.5, 2.0, 1.0, 3.0, **_BT)
+    A_ref, v_ref = _CHAR_CACHE["bt"]
+    vals = []
+    for mp in (321, 641):
+        p = W.Params(E_dc=1.0, E_omega=0.5, omega=2.0, B=1.0, mu=3.0, alpha=0.9496, n_max=24,
+                     m_points=mp, phiy_min=-8, phiy_max=8, dt=2e-3, periods=10.0,
+                     avg_window=1.0, **_BT)
+        r = oracle.solve(p, flags)
+        vals.append((r.A, r.v_dc))
+    A_ex = vals[1][0] - (vals[0][0] - vals[1][0]) / 3.0
+    v_ex = vals[1][1] - (vals[0][1] - vals[1][1]) / 3.0
+    return max(_rel(A_ex, A_ref) / 3e-4, _rel(v_ex, v_ref) / 3e-5)
+
+
+def test_characteristics_with_time_dependent_B():
+    assert pin_characteristics_bt() <= 1
+
+
+def test_constant_field_special_cases_of_B_t():
+    """B_omega = 0 is the paper's constant field, bit for bit; with omega = 0
+    the field is the constant B + B_omega cos(B_phase)."""
+    p = _conv_params(periods=2.0)
+    r0 = oracle.solve(p)
+    r1 = oracle.solve(p.replace(B_omega=0.0, B_phase=1.3))
+    assert r0.A == r1.A and r0.v_dc == r1.v_dc
+    q = W.Params(E_dc=1.3, E_omega=0.0, omega=0.0, B=0.8, mu=2.0, n_max=16, m_points=121,
+                 phiy_min=-8, phiy_max=8, dt=5e-3, t_max=2.0, avg_window=1.0)
+    s0 = oracle.solve(q.replace(B=0.8 + 0.5 * math.cos(0.9)))
+    s1 = oracle.solve(q.replace(B_omega=0.5, B_phase=0.9))
+    assert s0.v_dc == s1.v_dc and s0.norm_err == s1.norm_err
+
+
 def _f_from_harmonics(a, b, phix, m_idx):
     """f = sum_n a_n cos(n phi_x) + b_n sin(n phi_x) (Eq. f_fourier) at
     (phi_x, column m) pairs."""
@@ -422,9 +485,11 @@ MUTATIONS = {
     oracle.MUT_SIGMA0_ONE: [pin_equilibrium, pin_tucker],
     oracle.MUT_NO_CHI: [pin_stationary, pin_pdf_characteristics],
     oracle.MUT_STALE_SOURCE: [pin_order_dt],
-    oracle.MUT_THETA_START_ONLY: [pin_tucker, pin_b0_recurrence, pin_characteristics_ac],
+    oracle.MUT_THETA_START_ONLY: [pin_tucker, pin_b0_recurrence, pin_characteristics_ac,
+                                  pin_order_dt_bt],
     oracle.MUT_STENCIL_INDEX: [pin_sublattice, pin_pdf_characteristics],
     oracle.MUT_NO_B0_RESET: [pin_stationary],
+    oracle.MUT_B_STENCIL_START: [pin_order_dt_bt],
 }
 
 
