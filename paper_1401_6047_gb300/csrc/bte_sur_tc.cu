@@ -42,7 +42,8 @@ constexpr size_t kOffW0 = kOffH + kOpBytes;
 constexpr size_t kOffW1 = kOffW0 + kHalfBytes;
 constexpr size_t kOffX = kOffW1 + kHalfBytes;
 constexpr size_t kOffBias = kOffX + (size_t)TM * kIn * 4; /* b2, b3 */
-constexpr size_t kOffBar = kOffBias + 2 * (size_t)TH * 4;
+constexpr size_t kOffW4 = kOffBias + 2 * (size_t)TH * 4;  /* W4 [2][256], b4 [2] */
+constexpr size_t kOffBar = kOffW4 + (2 * (size_t)TH + 4) * 4;
 constexpr size_t kSmemTC = kOffBar + 64 + 1024; /* + alignment slack */
 
 /* silu(z) = z / (1 + exp(-z)), fast exponential and reciprocal (as in training) */
@@ -118,6 +119,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
     unsigned char* hS = tsm + kOffH;
     float* sx = reinterpret_cast<float*>(tsm + kOffX);
     float* sb = reinterpret_cast<float*>(tsm + kOffBias);
+    float* sw4 = reinterpret_cast<float*>(tsm + kOffW4);
     uint64_t* bars = reinterpret_cast<uint64_t*>(tsm + kOffBar); /* w0, w1, mma */
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tsm + kOffBar + 32);
     const uint32_t aH = dev::smem_u32(hS);
@@ -130,6 +132,21 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
     const float* P = a.params + mem * a.pstride;
     const unsigned char* Wg = reinterpret_cast<const unsigned char*>(a.wti) + (size_t)mem * 4 * kHalfBytes;
     bool ok = true;
+
+    /* every global parameter load of the CTA is issued here, so that their
+     * latencies overlap (layer-1 unit o of rows [64 rh, 64 rh + 64); biases of
+     * layers 2, 3 and the output layer's weights go to shared memory) */
+    const int o1 = tid & (TH - 1), rh1 = tid / TH;
+    float w1[kIn];
+#pragma unroll
+    for (int i = 0; i < kIn; ++i) w1[i] = P[a.off.W1 + (long long)o1 * kIn + i];
+    const float b1 = P[a.off.b1 + o1];
+    if (tid < TH) {
+        sb[tid] = P[a.off.b2 + tid];
+        sb[TH + tid] = P[a.off.b3 + tid];
+    }
+    sw4[tid] = P[a.off.W4 + tid]; /* 512 threads: both output rows */
+    if (tid < kOut) sw4[2 * TH + tid] = P[a.off.b4 + tid];
 
     if (tid == 0) {
         dev::mbar_init(bW[0], 1);
@@ -160,10 +177,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
         }
     };
     if (tid == 0) load_layer(0);
-    if (tid < TH) {
-        sb[tid] = P[a.off.b2 + tid];
-        sb[TH + tid] = P[a.off.b3 + tid];
-    }
 
     /* ---- layer 1 on the FP32 cores: h1 = silu(W1 xh + b1) ---- */
     for (int r = tid; r < TM; r += kThreadsTC) {
@@ -182,19 +195,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
         for (int i = 0; i < kIn; ++i) sx[r * kIn + i] = xh[i];
     }
     __syncthreads();
-    {
-        /* unit o of rows [64 rh, 64 rh + 64) */
-        const int o = tid & (TH - 1), rh = tid / TH;
-        float w[kIn];
+    for (int r = rh1 * (TM / 2); r < (rh1 + 1) * (TM / 2); ++r) {
+        float z = b1;
 #pragma unroll
-        for (int i = 0; i < kIn; ++i) w[i] = P[a.off.W1 + (long long)o * kIn + i];
-        const float b = P[a.off.b1 + o];
-        for (int r = rh * (TM / 2); r < (rh + 1) * (TM / 2); ++r) {
-            float z = b;
-#pragma unroll
-            for (int i = 0; i < kIn; ++i) z = fmaf(w[i], sx[r * kIn + i], z);
-            *reinterpret_cast<__nv_bfloat16*>(hS + canon(r, o)) = __float2bfloat16_rn(silu_tc(z));
-        }
+        for (int i = 0; i < kIn; ++i) z = fmaf(w1[i], sx[r * kIn + i], z);
+        *reinterpret_cast<__nv_bfloat16*>(hS + canon(r, o1)) = __float2bfloat16_rn(silu_tc(z));
     }
 
     /* ---- layers 2 and 3 ---- */
@@ -247,13 +252,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
     __syncthreads();
 
     /* ---- output layer (N = 2): one warp per row, lane c reads units 8c .. 8c+7 ---- */
-    float w0[8], w1[8];
+    float w40[8], w41[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        w0[i] = P[a.off.W4 + lane * 8 + i];
-        w1[i] = P[a.off.W4 + TH + lane * 8 + i];
+        w40[i] = sw4[lane * 8 + i];
+        w41[i] = sw4[TH + lane * 8 + i];
     }
-    const float b40 = P[a.off.b4], b41 = P[a.off.b4 + 1];
+    const float b40 = sw4[2 * TH], b41 = sw4[2 * TH + 1];
     for (int r = warp; r < TM; r += kThreadsTC / 32) {
         const uint4 raw = *reinterpret_cast<const uint4*>(hS + canon(r, lane * 8));
         const __nv_bfloat162* hp = reinterpret_cast<const __nv_bfloat162*>(&raw);
@@ -261,10 +266,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const float2 f = __bfloat1622float2(hp[i]);
-            y0 = fmaf(w0[2 * i], f.x, y0);
-            y0 = fmaf(w0[2 * i + 1], f.y, y0);
-            y1 = fmaf(w1[2 * i], f.x, y1);
-            y1 = fmaf(w1[2 * i + 1], f.y, y1);
+            y0 = fmaf(w40[2 * i], f.x, y0);
+            y0 = fmaf(w40[2 * i + 1], f.y, y0);
+            y1 = fmaf(w41[2 * i], f.x, y1);
+            y1 = fmaf(w41[2 * i + 1], f.y, y1);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
