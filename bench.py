@@ -734,16 +734,25 @@ def run_surrogate(args):
         pass
     peak = float(peaks.get("bf16_tflops", 1900.0))
 
-    # end to end: host inputs in, host mean / std / mask out
+    # end to end: host inputs in, host mean / std / mask out, through the
+    # public host-array call, page-locked host buffers (the library overlaps
+    # each chunk's copies with the next chunk's inference)
     e2e = None
     if not args.no_e2e:
-        x32 = np.ascontiguousarray(xs, dtype=np.float32)
+        xp = torch.empty((n, 5), dtype=torch.float32, pin_memory=True)
+        xp.numpy()[:] = np.asarray(xs, dtype=np.float32)
+        outs = (torch.empty((n, 2), dtype=torch.float32, pin_memory=True).numpy(),
+                torch.empty((n, 2), dtype=torch.float32, pin_memory=True).numpy(),
+                torch.empty(n, dtype=torch.uint8, pin_memory=True).numpy())
+        sur.predict(xp.numpy(), threshold=1e-3, out=outs)  # warm-up (creates the copy streams)
+        e2e_steps = max(1, min(args.steps, 3))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sur.predict(x32, threshold=1e-3)
-        el = time.perf_counter() - t0
+        for _ in range(e2e_steps):
+            sur.predict(xp.numpy(), threshold=1e-3, out=outs)
+        el = (time.perf_counter() - t0) / e2e_steps
         e2e = {"value": world * n / el, "unit": "points/s", "h2d_bytes_per_step": int(n * 20),
-               "d2h_bytes_per_step": int(n * 17)}
+               "d2h_bytes_per_step": int(n * 17), "host_buffers": "page-locked"}
 
     # accuracy on held-out solver results, and the hybrid against the solver alone
     mean, std, mask = sur.predict(x_ho, threshold=1e-3)

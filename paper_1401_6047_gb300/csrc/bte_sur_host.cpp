@@ -43,8 +43,13 @@ struct bte_sur {
     float *xd, *yd;
     long long nd;
     long long t; /* Adam steps taken */
-    float *xin, *mean_d, *std_d;
-    unsigned char* mask_d;
+    /* host-array inference: two buffer sets, so that the copies of one
+     * chunk overlap the inference of the other, on two copy streams */
+    float *xin[2], *mean_d[2], *std_d[2];
+    unsigned char* mask_d[2];
+    cudaStream_t cs_in, cs_out;
+    cudaEvent_t ev_in[2], ev_comp[2], ev_out[2];
+    bool pipe_ready;
 };
 
 namespace {
@@ -254,6 +259,19 @@ int predict_chunks(bte_sur* h, const float* x_dev, long long n, float* mean, flo
     return BTE_OK;
 }
 
+/* copy streams and events of the host-array inference, made on first use */
+int make_pipe(bte_sur* h) {
+    CU(cudaStreamCreateWithFlags(&h->cs_in, cudaStreamNonBlocking));
+    CU(cudaStreamCreateWithFlags(&h->cs_out, cudaStreamNonBlocking));
+    for (int s = 0; s < 2; ++s) {
+        CU(cudaEventCreateWithFlags(&h->ev_in[s], cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&h->ev_comp[s], cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&h->ev_out[s], cudaEventDisableTiming));
+    }
+    h->pipe_ready = true;
+    return BTE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -312,9 +330,13 @@ int bte_sur_create(const bte_sur_config* cfg, bte_sur** out) {
     const size_t opart = take((size_t)M * (cap / 128) * nred * 4);
     const size_t oloss = take((size_t)M * 8);
     const size_t oidx = take((size_t)M * cap * 4);
-    const size_t oxin = take((size_t)cap * kIn * 4);
-    const size_t omean = take((size_t)cap * kOut * 4), ostd = take((size_t)cap * kOut * 4);
-    const size_t omask = take((size_t)cap);
+    size_t oxin[2], omean[2], ostd[2], omask[2];
+    for (int s = 0; s < 2; ++s) {
+        oxin[s] = take((size_t)cap * kIn * 4);
+        omean[s] = take((size_t)cap * kOut * 4);
+        ostd[s] = take((size_t)cap * kOut * 4);
+        omask[s] = take((size_t)cap);
+    }
     cudaError_t e = cudaMalloc(&h->mem, o);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -343,10 +365,12 @@ int bte_sur_create(const bte_sur_config* cfg, bte_sur** out) {
     h->partial = (float*)(b + opart);
     h->loss = (double*)(b + oloss);
     h->idx = (int*)(b + oidx);
-    h->xin = (float*)(b + oxin);
-    h->mean_d = (float*)(b + omean);
-    h->std_d = (float*)(b + ostd);
-    h->mask_d = (unsigned char*)(b + omask);
+    for (int s = 0; s < 2; ++s) {
+        h->xin[s] = (float*)(b + oxin[s]);
+        h->mean_d[s] = (float*)(b + omean[s]);
+        h->std_d[s] = (float*)(b + ostd[s]);
+        h->mask_d[s] = (unsigned char*)(b + omask[s]);
+    }
     if (cfg->stream) {
         h->stream = (cudaStream_t)cfg->stream;
     } else {
@@ -493,17 +517,41 @@ int bte_sur_predict_device(bte_sur* h, const float* x, int64_t n, float* mean, f
 int bte_sur_predict(bte_sur* h, const float* x, int64_t n, float* mean, float* stdv, uint8_t* mask,
                     double threshold) {
     if (!h || !x || !mean || !stdv || n < 0) return fail(BTE_EINVAL, "bad argument");
-    for (long long r0 = 0; r0 < n; r0 += h->cap) {
-        const long long rows = std::min<long long>(h->cap, n - r0);
-        CU(cudaMemcpyAsync(h->xin, x + r0 * kIn, rows * kIn * 4, cudaMemcpyHostToDevice, h->stream));
-        int rc = predict_chunks(h, h->xin, rows, h->mean_d, h->std_d, mask ? h->mask_d : nullptr,
-                                threshold);
+    if (n == 0) return BTE_OK;
+    if (!h->pipe_ready) {
+        int rc = make_pipe(h);
         if (rc) return rc;
-        CU(cudaMemcpyAsync(mean + r0 * kOut, h->mean_d, rows * kOut * 4, cudaMemcpyDeviceToHost, h->stream));
-        CU(cudaMemcpyAsync(stdv + r0 * kOut, h->std_d, rows * kOut * 4, cudaMemcpyDeviceToHost, h->stream));
-        if (mask) CU(cudaMemcpyAsync(mask + r0, h->mask_d, rows, cudaMemcpyDeviceToHost, h->stream));
-        CU(cudaStreamSynchronize(h->stream));
     }
+    /* chunk i uses buffer set i & 1: its input copy waits until the
+     * inference of chunk i-2 has read that set, its inference waits for its
+     * input and for the output copies of chunk i-2, its output copies wait
+     * for its inference (stream order does the rest) */
+    long long i = 0;
+    for (long long r0 = 0; r0 < n; r0 += h->cap, ++i) {
+        const int s = (int)(i & 1);
+        const long long rows = std::min<long long>(h->cap, n - r0);
+        if (i >= 2) CU(cudaStreamWaitEvent(h->cs_in, h->ev_comp[s], 0));
+        CU(cudaMemcpyAsync(h->xin[s], x + r0 * kIn, rows * kIn * 4, cudaMemcpyHostToDevice, h->cs_in));
+        CU(cudaEventRecord(h->ev_in[s], h->cs_in));
+        CU(cudaStreamWaitEvent(h->stream, h->ev_in[s], 0));
+        if (i >= 2) CU(cudaStreamWaitEvent(h->stream, h->ev_out[s], 0));
+        int rc = predict_chunks(h, h->xin[s], rows, h->mean_d[s], h->std_d[s],
+                                mask ? h->mask_d[s] : nullptr, threshold);
+        if (rc) {
+            cudaStreamSynchronize(h->cs_in);
+            cudaStreamSynchronize(h->stream);
+            cudaStreamSynchronize(h->cs_out);
+            return rc;
+        }
+        CU(cudaEventRecord(h->ev_comp[s], h->stream));
+        CU(cudaStreamWaitEvent(h->cs_out, h->ev_comp[s], 0));
+        CU(cudaMemcpyAsync(mean + r0 * kOut, h->mean_d[s], rows * kOut * 4, cudaMemcpyDeviceToHost, h->cs_out));
+        CU(cudaMemcpyAsync(stdv + r0 * kOut, h->std_d[s], rows * kOut * 4, cudaMemcpyDeviceToHost, h->cs_out));
+        if (mask) CU(cudaMemcpyAsync(mask + r0, h->mask_d[s], rows, cudaMemcpyDeviceToHost, h->cs_out));
+        CU(cudaEventRecord(h->ev_out[s], h->cs_out));
+    }
+    CU(cudaStreamSynchronize(h->cs_out));
+    CU(cudaStreamSynchronize(h->stream));
     int err = 0;
     CU(cudaMemcpy(&err, h->err, sizeof err, cudaMemcpyDeviceToHost));
     if (err) return fail(BTE_ETIMEOUT, "a bounded wait in the inference kernel gave up");
@@ -580,6 +628,14 @@ int bte_sur_hybrid(bte_sur* h, const double* x, int64_t n, double threshold, int
 void bte_sur_destroy(bte_sur* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    for (cudaStream_t* cs : {&h->cs_in, &h->cs_out})
+        if (*cs) {
+            cudaStreamSynchronize(*cs);
+            cudaStreamDestroy(*cs);
+        }
+    for (int s = 0; s < 2; ++s)
+        for (cudaEvent_t ev : {h->ev_in[s], h->ev_comp[s], h->ev_out[s]})
+            if (ev) cudaEventDestroy(ev);
     if (h->xd) cudaFree(h->xd);
     if (h->mem) cudaFree(h->mem);
     if (h->own_stream) cudaStreamDestroy(h->stream);

@@ -205,16 +205,27 @@ class Surrogate:
                                           _p(g, ctypes.c_float), _p(loss, ctypes.c_double)))
         return loss, g
 
-    def predict(self, x, threshold: float = 1e-3):
+    def predict(self, x, threshold: float = 1e-3, out=None):
+        """(mean [n, 2], std [n, 2], mask [n] bool) of host inputs x [n, 5].
+        `out` = (mean float32 [n, 2], std float32 [n, 2], mask uint8 [n]) host
+        arrays to fill instead (page-locked ones let the copies overlap the
+        inference); the mask is then returned as the uint8 array itself."""
         x = _f32(x)
         n = x.shape[0]
-        mean = np.zeros((n, 2), dtype=np.float32)
-        std = np.zeros((n, 2), dtype=np.float32)
-        mask = np.zeros(n, dtype=np.uint8)
+        if out is None:
+            mean = np.zeros((n, 2), dtype=np.float32)
+            std = np.zeros((n, 2), dtype=np.float32)
+            mask = np.zeros(n, dtype=np.uint8)
+        else:
+            mean, std, mask = out
+            for a, shp, dt in ((mean, (n, 2), np.float32), (std, (n, 2), np.float32),
+                               (mask, (n,), np.uint8)):
+                if a.shape != shp or a.dtype != dt or not a.flags["C_CONTIGUOUS"]:
+                    raise ValueError("out arrays must be C-contiguous float32 [n, 2] x 2 and uint8 [n]")
         bte._check(self._lib.bte_sur_predict(self._h, _p(x, ctypes.c_float), n, _p(mean, ctypes.c_float),
                                              _p(std, ctypes.c_float), _p(mask, ctypes.c_uint8),
                                              float(threshold)))
-        return mean, std, mask.astype(bool)
+        return (mean, std, mask.astype(bool)) if out is None else (mean, std, mask)
 
     def predict_device(self, x_ptr: int, n: int, mean_ptr: int, std_ptr: int, mask_ptr: int = 0,
                        threshold: float = 1e-3) -> None:

@@ -134,6 +134,37 @@ def test_device_prediction_equals_host_prediction():
     assert np.array_equal(kd.cpu().numpy().astype(bool), mask)
 
 
+def test_pipelined_host_prediction_over_many_chunks():
+    """The host-array call alternates two buffer sets over six chunks (copies
+    of one chunk overlapping the inference of the next): bit for bit the
+    device-array result, with pageable and with page-locked host arrays,
+    and again on a second call."""
+    torch = pytest.importorskip("torch")
+    p = S.init_params(3, seed=6)
+    n = 1357  # 5 full chunks of 256 and a ragged sixth
+    x = W.sweep_matrix(n, 12).astype(np.float32)
+    with S.Surrogate(Y_MEAN, Y_STD, members=3, batch_capacity=256) as sur:
+        sur.set_params(p)
+        xd = torch.from_numpy(x).cuda()
+        md = torch.zeros((n, 2), device="cuda")
+        sd = torch.zeros((n, 2), device="cuda")
+        kd = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        sur.predict_device(xd.data_ptr(), n, md.data_ptr(), sd.data_ptr(), kd.data_ptr(), 1e-2)
+        torch.cuda.synchronize()
+        ref = (md.cpu().numpy(), sd.cpu().numpy(), kd.cpu().numpy())
+        mean, std, mask = sur.predict(x, threshold=1e-2)
+        assert np.array_equal(mean, ref[0]) and np.array_equal(std, ref[1])
+        assert np.array_equal(mask, ref[2].astype(bool))
+        xp = torch.from_numpy(x).pin_memory()
+        outs = (torch.zeros((n, 2)).pin_memory().numpy(), torch.zeros((n, 2)).pin_memory().numpy(),
+                torch.zeros(n, dtype=torch.uint8).pin_memory().numpy())
+        for _ in range(2):
+            outs[0][:] = 0
+            m2, s2, k2 = sur.predict(xp.numpy(), threshold=1e-2, out=outs)
+            assert np.array_equal(m2, ref[0]) and np.array_equal(s2, ref[1])
+            assert np.array_equal(k2, ref[2])
+
+
 def test_hybrid_uses_the_solver_exactly_where_members_disagree():
     p = S.init_params(4, seed=6)
     x = W.sweep_matrix(10, 13)
