@@ -134,13 +134,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
     bool ok = true;
 
     /* every global parameter load of the CTA is issued here, so that their
-     * latencies overlap (layer-1 unit o of rows [64 rh, 64 rh + 64); biases of
-     * layers 2, 3 and the output layer's weights go to shared memory) */
-    const int o1 = tid & (TH - 1), rh1 = tid / TH;
-    float w1[kIn];
+     * latencies overlap (biases of layers 2, 3 and the output layer's weights
+     * go to shared memory).  Layer 1: the thread computes units
+     * 8 ug1 .. 8 ug1 + 7 of rows 8 (rb1 + 2k) + (lane & 7), k = 0..7, so
+     * that a quarter-warp writes one 8 x 8 core matrix (128 contiguous bytes)
+     * with one 16-byte store per lane. */
+    const int q1 = 4 * warp + (lane >> 3);
+    const int ug1 = q1 & 31, rb1 = q1 >> 5;
+    float w1[8][kIn], b1[8];
 #pragma unroll
-    for (int i = 0; i < kIn; ++i) w1[i] = P[a.off.W1 + (long long)o1 * kIn + i];
-    const float b1 = P[a.off.b1 + o1];
+    for (int u = 0; u < 8; ++u) {
+#pragma unroll
+        for (int i = 0; i < kIn; ++i) w1[u][i] = P[a.off.W1 + (long long)(8 * ug1 + u) * kIn + i];
+        b1[u] = P[a.off.b1 + 8 * ug1 + u];
+    }
     if (tid < TH) {
         sb[tid] = P[a.off.b2 + tid];
         sb[TH + tid] = P[a.off.b3 + tid];
@@ -195,11 +202,24 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
         for (int i = 0; i < kIn; ++i) sx[r * kIn + i] = xh[i];
     }
     __syncthreads();
-    for (int r = rh1 * (TM / 2); r < (rh1 + 1) * (TM / 2); ++r) {
-        float z = b1;
+#pragma unroll 1
+    for (int k = 0; k < TM / 16; ++k) {
+        const int r = 8 * (rb1 + 2 * k) + (lane & 7);
+        float xv[kIn];
 #pragma unroll
-        for (int i = 0; i < kIn; ++i) z = fmaf(w1[i], sx[r * kIn + i], z);
-        *reinterpret_cast<__nv_bfloat16*>(hS + canon(r, o1)) = __float2bfloat16_rn(silu_tc(z));
+        for (int i = 0; i < kIn; ++i) xv[i] = sx[r * kIn + i];
+        __nv_bfloat162 pk[4];
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            float z0 = b1[u], z1 = b1[u + 1];
+#pragma unroll
+            for (int i = 0; i < kIn; ++i) {
+                z0 = fmaf(w1[u][i], xv[i], z0);
+                z1 = fmaf(w1[u + 1][i], xv[i], z1);
+            }
+            pk[u / 2] = __floats2bfloat162_rn(silu_tc(z0), silu_tc(z1));
+        }
+        *reinterpret_cast<uint4*>(hS + canon(r, 8 * ug1)) = *reinterpret_cast<const uint4*>(pk);
     }
 
     /* ---- layers 2 and 3 ---- */
