@@ -2,7 +2,7 @@
 
 An 8-member ensemble is trained on the committed training set (points of
 the sweep box solved by the batched solver under the surrogate protocol)
-and judged on held-out points solved the same way.  The surrogate with
+and assessed on held-out points solved the same way.  The surrogate with
 solver fallback (threshold 1e-3 on the ensemble standard deviation) must
 (1) keep the points it answers itself close to the solver, and (2) finish
 a held-out sample faster than the solver alone.
