@@ -1,7 +1,7 @@
 /*
  * bte_sur_host.cpp -- host side of the surrogate ABI (include/bte_surrogate.h):
  * device buffers of the ensemble, the launch sequence of one training step
- * and of inference, and the surrogate-with-solver-fallback driver.  All
+ * and of inference, and the surrogate-with-solver-fallback routine.  All
  * arithmetic runs in the kernels of bte_sur_kernels.cu (and, for fallback
  * points, in the batched solver).
  */
