@@ -83,7 +83,11 @@ BTE_API int bte_sur_grad(bte_sur* h, const float* x, const float* t, int32_t n, 
 /* Ensemble prediction of HOST x [n][5]: mean and population standard
  * deviation over members of the de-standardised outputs (HOST [n][2] each)
  * and, when mask is not NULL, mask[i] = 1 where max(std[i][0], std[i][1]) >
- * threshold (or is NaN), else 0. */
+ * threshold (or is NaN), else 0.  Works in chunks of batch_capacity rows
+ * over two device buffer sets: the copies of one chunk (on two internal
+ * copy streams, created on the first call) overlap the inference of the
+ * next; with page-locked host arrays the copies are fully asynchronous.
+ * Returns when every output is written. */
 BTE_API int bte_sur_predict(bte_sur* h, const float* x, int64_t n, float* mean, float* stdv,
                             uint8_t* mask, double threshold);
 
