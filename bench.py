@@ -418,7 +418,7 @@ def sweep_launches(pts, max_batch, max_bytes, elem, tile, chunk, graph_len, tier
             _, P, _, _ = bte.time_grid(p)
             ntx = -(-p.m_points // tile)
             pitch = -(-(128 // elem + ntx * tile + 32 // elem) // 32) * 32
-            sb = 4 * (p.n_max + 1) * pitch * elem + 2 * (P + 2) * 8 + 4096
+            sb = 4 * (p.n_max + 1) * pitch * elem + 6 * (P + 2) * elem + 4096
             if sizes and byt + sb > max_bytes:
                 n += len(sizes)
                 byt, sizes = 0, set()
@@ -440,7 +440,7 @@ def sweep_launches(pts, max_batch, max_bytes, elem, tile, chunk, graph_len, tier
             K, P, p = info[j]
             ntx = -(-p.m_points // tile)
             pitch = -(-(128 // elem + ntx * tile + 32 // elem) // 32) * 32
-            sb = 8 * (p.n_max + 1) * pitch * elem + 2 * (P + 2) * 8 + 4096
+            sb = 8 * (p.n_max + 1) * pitch * elem + 6 * (P + 2) * elem + 4096
             if j > i and byt + sb > max_bytes:
                 break
             byt += sb

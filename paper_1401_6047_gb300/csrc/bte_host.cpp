@@ -1074,7 +1074,8 @@ int bte_batch_run(const bte_params* p, int32_t n, bte_obs* out, const bte_batch_
                (resC > 0 || (int)(last - first) < max_batch)) {
             const BatchPoint& b = pts[last];
             const long long pitch = (long long)align_up((size_t)(128 / elem + b.ntx * tile + 32 / elem), 32);
-            const long long sb = (resC > 0 ? 4ll : 8ll) * b.N1 * pitch * elem + 2ll * (b.tg.P + 2) * 8 + 4096;
+            /* state arrays, the two [3][P+2] drive tables, other tables */
+            const long long sb = (resC > 0 ? 4ll : 8ll) * b.N1 * pitch * elem + 6ll * (b.tg.P + 2) * elem + 4096;
             if (last > first && bytes + sb > max_bytes) break;
             bytes += sb;
             ++last;
