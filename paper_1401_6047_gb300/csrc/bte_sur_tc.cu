@@ -2,9 +2,10 @@
  * bte_sur_tc.cu -- ensemble inference of the surrogate MLP on the fifth-
  * generation tensor cores (tcgen05, sm_103a).
  *
- * One CTA takes 128 rows of one member.  The 5-input layer runs on the FP32
- * cores and writes h1 (BF16) into shared memory in the tensor cores'
- * canonical K-major layout (8 x 8 core matrices, no swizzle).  Each 256 x 256
+ * One CTA takes two 128-row tiles of one member, one after the other.  The
+ * 5-input layer runs on the FP32 cores and writes h1 (BF16) into shared
+ * memory in the tensor cores' canonical K-major layout (8 x 8 core
+ * matrices, no swizzle).  Each 256 x 256
  * layer is 2 x 16 tcgen05.mma instructions (M = 128, N = 128, K = 16, BF16
  * in, FP32 accumulate) issued by one thread into 256 columns of tensor
  * memory; the weight halves (64 KB each) arrive by bulk copy into two
@@ -32,6 +33,7 @@ constexpr int TH = 256;             /* hidden width */
 constexpr int TN = 128;             /* MMA N (one weight half) */
 constexpr int TK = 16;              /* MMA K */
 constexpr int kThreadsTC = 512; /* 16 warps: 4 per tensor-memory lane quadrant */
+constexpr int kTPC = 2;         /* row tiles per CTA, one after another */
 constexpr uint32_t kHalfBytes = (uint32_t)TN * TH * 2; /* 64 KB */
 constexpr uint32_t kOpBytes = (uint32_t)TM * TH * 2;   /* 64 KB */
 constexpr uint32_t kCoreStride = 128;                  /* bytes of one 8 x 8 core matrix */
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
     const uint32_t bW[2] = {dev::smem_u32(&bars[0]), dev::smem_u32(&bars[1])};
     const uint32_t bM = dev::smem_u32(&bars[2]);
 
-    const int mem = blockIdx.y, r0 = blockIdx.x * TM;
+    const int mem = blockIdx.y, ntile = a.Bp / TM;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float* P = a.params + mem * a.pstride;
     const unsigned char* Wg = reinterpret_cast<const unsigned char*>(a.wti) + (size_t)mem * 4 * kHalfBytes;
@@ -184,6 +186,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
         }
     };
     if (tid == 0) load_layer(0);
+
+    /* the CTA's row tiles, one after another with the same member: set-up,
+     * tensor memory and the small parameters serve both, and the next
+     * tile's first weight layer streams in under this tile's last
+     * epilogue.  Each barrier completes once per layer, so its wait parity
+     * is the layer index in every tile. */
+    for (int it = 0; it < kTPC; ++it) {
+    const int tile = blockIdx.x * kTPC + it;
+    if (tile >= ntile) break;
+    const int r0 = tile * TM;
 
     /* ---- layer 1 on the FP32 cores: h1 = silu(W1 xh + b1) ---- */
     for (int r = tid; r < TM; r += kThreadsTC) {
@@ -248,6 +260,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
         tc_fence_after();
         /* the weight buffers are free: fetch the next layer's */
         if (tid == 0 && l == 0) load_layer(1);
+        if (tid == 0 && l == 1 && it + 1 < kTPC && tile + 1 < ntile) load_layer(0);
         /* epilogue: bias + SiLU, BF16, written as the next operand (row = TMEM lane) */
         const float* bias = sb + l * TH;
         const int row = sub * 32 + lane;
@@ -302,6 +315,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
             a.Yh[yo + 1] = y1 + b41;
         }
     }
+    __syncthreads(); /* h and the inputs are free for the next tile */
+    }
     if (!ok) atomicExch(a.err, 1);
     tc_fence_after();
     if (warp == 0)
@@ -340,7 +355,7 @@ int launch_infer_tc(const InferArgs& a, int members, void* stream) {
     cudaError_t e = cudaFuncSetAttribute(infer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmemTC);
     if (e != cudaSuccess) return (int)e;
-    const dim3 grid(a.Bp / TM, members);
+    const dim3 grid((a.Bp / TM + kTPC - 1) / kTPC, members);
     infer_tc_kernel<<<grid, kThreadsTC, kSmemTC, (cudaStream_t)stream>>>(a);
     e = cudaGetLastError();
     return e == cudaSuccess ? 0 : (int)e;
