@@ -193,129 +193,131 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
      * epilogue.  Each barrier completes once per layer, so its wait parity
      * is the layer index in every tile. */
     for (int it = 0; it < kTPC; ++it) {
-    const int tile = blockIdx.x * kTPC + it;
-    if (tile >= ntile) break;
-    const int r0 = tile * TM;
+        const int tile = blockIdx.x * kTPC + it;
+        if (tile >= ntile) break;
+        const int r0 = tile * TM;
 
-    /* ---- layer 1 on the FP32 cores: h1 = silu(W1 xh + b1) ---- */
-    for (int r = tid; r < TM; r += kThreadsTC) {
-        const int row = r0 + r;
-        float xh[kIn];
-        if (row < a.nvalid) {
-            const long long s = a.row0 + row;
-#pragma unroll
-            for (int i = 0; i < kIn; ++i)
-                xh[i] = 2.0f * (a.x[s * kIn + i] - a.sc.x_lo[i]) * a.sc.x_inv[i] - 1.0f;
-        } else {
-#pragma unroll
-            for (int i = 0; i < kIn; ++i) xh[i] = 0.0f;
-        }
-#pragma unroll
-        for (int i = 0; i < kIn; ++i) sx[r * kIn + i] = xh[i];
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int k = 0; k < TM / 16; ++k) {
-        const int r = 8 * (rb1 + 2 * k) + (lane & 7);
-        float xv[kIn];
-#pragma unroll
-        for (int i = 0; i < kIn; ++i) xv[i] = sx[r * kIn + i];
-        __nv_bfloat162 pk[4];
-#pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-            float z0 = b1[u], z1 = b1[u + 1];
-#pragma unroll
-            for (int i = 0; i < kIn; ++i) {
-                z0 = fmaf(w1[u][i], xv[i], z0);
-                z1 = fmaf(w1[u + 1][i], xv[i], z1);
+        /* ---- layer 1 on the FP32 cores: h1 = silu(W1 xh + b1) ---- */
+        for (int r = tid; r < TM; r += kThreadsTC) {
+            const int row = r0 + r;
+            float xh[kIn];
+            if (row < a.nvalid) {
+                const long long s = a.row0 + row;
+    #pragma unroll
+                for (int i = 0; i < kIn; ++i)
+                    xh[i] = 2.0f * (a.x[s * kIn + i] - a.sc.x_lo[i]) * a.sc.x_inv[i] - 1.0f;
+            } else {
+    #pragma unroll
+                for (int i = 0; i < kIn; ++i) xh[i] = 0.0f;
             }
-            pk[u / 2] = __floats2bfloat162_rn(silu_tc(z0), silu_tc(z1));
+    #pragma unroll
+            for (int i = 0; i < kIn; ++i) sx[r * kIn + i] = xh[i];
         }
-        *reinterpret_cast<uint4*>(hS + canon(r, 8 * ug1)) = *reinterpret_cast<const uint4*>(pk);
-    }
+        __syncthreads();
+    #pragma unroll 1
+        for (int k = 0; k < TM / 16; ++k) {
+            const int r = 8 * (rb1 + 2 * k) + (lane & 7);
+            float xv[kIn];
+    #pragma unroll
+            for (int i = 0; i < kIn; ++i) xv[i] = sx[r * kIn + i];
+            __nv_bfloat162 pk[4];
+    #pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                float z0 = b1[u], z1 = b1[u + 1];
+    #pragma unroll
+                for (int i = 0; i < kIn; ++i) {
+                    z0 = fmaf(w1[u][i], xv[i], z0);
+                    z1 = fmaf(w1[u + 1][i], xv[i], z1);
+                }
+                pk[u / 2] = __floats2bfloat162_rn(silu_tc(z0), silu_tc(z1));
+            }
+            *reinterpret_cast<uint4*>(hS + canon(r, 8 * ug1)) = *reinterpret_cast<const uint4*>(pk);
+        }
 
-    /* ---- layers 2 and 3 ---- */
-    constexpr uint32_t idesc = instr_desc(TM, TN);
-    const int sub = warp & 3;             /* TMEM lanes 32 sub .. 32 sub + 31 */
-    const int cq = warp >> 2;             /* accumulator columns 64 cq .. 64 cq + 63 */
-    for (int l = 0; l < 2; ++l) {
-        /* operand written by the generic proxy -> visible to the tensor cores */
-        dev::fence_proxy_async_smem();
+        /* ---- layers 2 and 3 ---- */
+        constexpr uint32_t idesc = instr_desc(TM, TN);
+        const int sub = warp & 3;             /* TMEM lanes 32 sub .. 32 sub + 31 */
+        const int cq = warp >> 2;             /* accumulator columns 64 cq .. 64 cq + 63 */
+        for (int l = 0; l < 2; ++l) {
+            /* operand written by the generic proxy -> visible to the tensor cores */
+            dev::fence_proxy_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (tid == 0) {
+                for (int hh = 0; hh < 2; ++hh)
+                    if (!dev::mbar_wait(bW[hh], (uint32_t)l)) ok = false;
+                tc_fence_after();
+                for (int hh = 0; hh < 2; ++hh)
+                    for (int ks = 0; ks < TH / TK; ++ks) {
+                        const uint64_t ad = smem_desc(aH + ks * 2 * kCoreStride, kCoreStride, kGroupStride);
+                        const uint64_t bd =
+                            smem_desc(aW[hh] + ks * 2 * kCoreStride, kCoreStride, kGroupStride);
+                        tc_mma(tmem + hh * TN, ad, bd, idesc, ks > 0 ? 1u : 0u);
+                    }
+                tc_commit(bM);
+            }
+            if (!dev::mbar_wait(bM, (uint32_t)l)) ok = false;
+            tc_fence_after();
+            /* the weight buffers are free: fetch the next layer's */
+            if (tid == 0 && l == 0) load_layer(1);
+            if (tid == 0 && l == 1 && it + 1 < kTPC && tile + 1 < ntile) load_layer(0);
+            /* epilogue: bias + SiLU, BF16, written as the next operand (row = TMEM lane) */
+            const float* bias = sb + l * TH;
+            const int row = sub * 32 + lane;
+            for (int cb = 0; cb < TH / 4; cb += 32) {
+                const int col0 = cq * (TH / 4) + cb;
+                float v[32];
+                tc_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)col0, v);
+    #pragma unroll
+                for (int c8 = 0; c8 < 32; c8 += 8) {
+                    __nv_bfloat162 pk[4];
+    #pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int col = col0 + c8 + 2 * e;
+                        pk[e] = __floats2bfloat162_rn(silu_tc(v[c8 + 2 * e] + bias[col]),
+                                                      silu_tc(v[c8 + 2 * e + 1] + bias[col + 1]));
+                    }
+                    *reinterpret_cast<uint4*>(hS + canon(row, col0 + c8)) =
+                        *reinterpret_cast<const uint4*>(pk);
+                }
+            }
+        }
         tc_fence_before();
         __syncthreads();
-        tc_fence_after();
-        if (tid == 0) {
-            for (int hh = 0; hh < 2; ++hh)
-                if (!dev::mbar_wait(bW[hh], (uint32_t)l)) ok = false;
-            tc_fence_after();
-            for (int hh = 0; hh < 2; ++hh)
-                for (int ks = 0; ks < TH / TK; ++ks) {
-                    const uint64_t ad = smem_desc(aH + ks * 2 * kCoreStride, kCoreStride, kGroupStride);
-                    const uint64_t bd = smem_desc(aW[hh] + ks * 2 * kCoreStride, kCoreStride, kGroupStride);
-                    tc_mma(tmem + hh * TN, ad, bd, idesc, ks > 0 ? 1u : 0u);
-                }
-            tc_commit(bM);
+
+        /* ---- output layer (N = 2): one warp per row, lane c reads units 8c .. 8c+7 ---- */
+        float w40[8], w41[8];
+    #pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            w40[i] = sw4[lane * 8 + i];
+            w41[i] = sw4[TH + lane * 8 + i];
         }
-        if (!dev::mbar_wait(bM, (uint32_t)l)) ok = false;
-        tc_fence_after();
-        /* the weight buffers are free: fetch the next layer's */
-        if (tid == 0 && l == 0) load_layer(1);
-        if (tid == 0 && l == 1 && it + 1 < kTPC && tile + 1 < ntile) load_layer(0);
-        /* epilogue: bias + SiLU, BF16, written as the next operand (row = TMEM lane) */
-        const float* bias = sb + l * TH;
-        const int row = sub * 32 + lane;
-        for (int cb = 0; cb < TH / 4; cb += 32) {
-            const int col0 = cq * (TH / 4) + cb;
-            float v[32];
-            tc_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)col0, v);
-#pragma unroll
-            for (int c8 = 0; c8 < 32; c8 += 8) {
-                __nv_bfloat162 pk[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int col = col0 + c8 + 2 * e;
-                    pk[e] = __floats2bfloat162_rn(silu_tc(v[c8 + 2 * e] + bias[col]),
-                                                  silu_tc(v[c8 + 2 * e + 1] + bias[col + 1]));
-                }
-                *reinterpret_cast<uint4*>(hS + canon(row, col0 + c8)) = *reinterpret_cast<const uint4*>(pk);
+        const float b40 = sw4[2 * TH], b41 = sw4[2 * TH + 1];
+        for (int r = warp; r < TM; r += kThreadsTC / 32) {
+            const uint4 raw = *reinterpret_cast<const uint4*>(hS + canon(r, lane * 8));
+            const __nv_bfloat162* hp = reinterpret_cast<const __nv_bfloat162*>(&raw);
+            float y0 = 0.0f, y1 = 0.0f;
+    #pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float2 f = __bfloat1622float2(hp[i]);
+                y0 = fmaf(w40[2 * i], f.x, y0);
+                y0 = fmaf(w40[2 * i + 1], f.y, y0);
+                y1 = fmaf(w41[2 * i], f.x, y1);
+                y1 = fmaf(w41[2 * i + 1], f.y, y1);
+            }
+    #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+                y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+            }
+            if (lane == 0) {
+                const long long yo = ((long long)mem * a.Bp + r0 + r) * kOut;
+                a.Yh[yo] = y0 + b40;
+                a.Yh[yo + 1] = y1 + b41;
             }
         }
-    }
-    tc_fence_before();
-    __syncthreads();
-
-    /* ---- output layer (N = 2): one warp per row, lane c reads units 8c .. 8c+7 ---- */
-    float w40[8], w41[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        w40[i] = sw4[lane * 8 + i];
-        w41[i] = sw4[TH + lane * 8 + i];
-    }
-    const float b40 = sw4[2 * TH], b41 = sw4[2 * TH + 1];
-    for (int r = warp; r < TM; r += kThreadsTC / 32) {
-        const uint4 raw = *reinterpret_cast<const uint4*>(hS + canon(r, lane * 8));
-        const __nv_bfloat162* hp = reinterpret_cast<const __nv_bfloat162*>(&raw);
-        float y0 = 0.0f, y1 = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float2 f = __bfloat1622float2(hp[i]);
-            y0 = fmaf(w40[2 * i], f.x, y0);
-            y0 = fmaf(w40[2 * i + 1], f.y, y0);
-            y1 = fmaf(w41[2 * i], f.x, y1);
-            y1 = fmaf(w41[2 * i + 1], f.y, y1);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            y0 += __shfl_xor_sync(0xffffffffu, y0, o);
-            y1 += __shfl_xor_sync(0xffffffffu, y1, o);
-        }
-        if (lane == 0) {
-            const long long yo = ((long long)mem * a.Bp + r0 + r) * kOut;
-            a.Yh[yo] = y0 + b40;
-            a.Yh[yo + 1] = y1 + b41;
-        }
-    }
-    __syncthreads(); /* h and the inputs are free for the next tile */
+        __syncthreads(); /* h and the inputs are free for the next tile */
     }
     if (!ok) atomicExch(a.err, 1);
     tc_fence_after();
