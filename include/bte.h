@@ -116,6 +116,16 @@ typedef struct {
     int32_t chunk_n;     /* harmonic rows per work item (>= 4)               */
     int32_t graph_steps; /* steps captured per CUDA graph replay (0 = auto)  */
     int32_t vec;         /* phi_y columns per thread: 2 or 4 (FP64: 2)      */
+    int32_t resident;    /* 1: keep the grid on chip -- all four arrays in the
+                            shared memory of one thread-block cluster of C
+                            CTAs (the largest C in 16, 8, 4, 2, 1 that leaves
+                            every CTA at least two harmonic rows and fits
+                            232,448 bytes per CTA), each bte_step/bte_run call
+                            one persistent launch that advances the state in
+                            place (the kernel of the batched run's on-chip
+                            tier); BTE_EINVAL when the grid does not fit.
+                            0: one fused step kernel launch per step.      */
+    int32_t reserved;    /* must be 0                                      */
 } bte_tuning;
 
 typedef struct bte_handle bte_handle;

@@ -177,16 +177,47 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
     int G, H, pitch, tile_m, chunk_n, vec, ts, ntx, nty;
+    int resC;                 /* on-chip mode: CTAs of the cluster, 0 = streamed */
+    size_t res_smem, res_arrays; /* its shared memory per CTA, and the arrays' part */
     size_t elem;
     size_t off_state[8];
     size_t off_row_a0, off_col_g, off_col_phi, off_ew, off_ef, off_tv, off_tn, off_part,
-        off_ticket, off_err, off_base, off_fin, total;
+        off_ticket, off_err, off_base, off_fin, off_res, total;
 };
 
+/* bytes of the on-chip mode's device record: the point's BatchInst, its
+ * order entry and queue counter, and the kernel's window-sum scratch */
+constexpr size_t kResBytes = 1024;
+constexpr int kResThreads = 512; /* threads per CTA of the on-chip kernel */
+
 int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L) {
+    if (t && t->reserved) return fail(BTE_EINVAL, "tuning.reserved must be 0");
+    if (t && (t->resident < 0 || t->resident > 1)) return fail(BTE_EINVAL, "tuning.resident must be 0 or 1");
     int rc = pick_tile(p, t, L.tile_m, L.chunk_n, L.vec);
     if (rc) return rc;
     L.elem = p->precision == BTE_FP64 ? 8 : 4;
+    /* on-chip mode: the largest cluster that leaves every CTA two rows and fits */
+    L.resC = 0;
+    L.res_smem = L.res_arrays = 0;
+    if (t && t->resident) {
+        const int N1 = p->n_max + 1;
+        for (int C = 16; C >= 1; C /= 2) {
+            if (C > 1 && (N1 + C - 1) / C < 2) continue;
+            size_t arrays = 0;
+            const size_t need = L.elem == 8
+                                    ? bte::resident_smem_bytes<double>(p->n_max, p->m_points - 1, C, &arrays)
+                                    : bte::resident_smem_bytes<float>(p->n_max, p->m_points - 1, C, &arrays);
+            if (need <= 232448) {
+                L.resC = C;
+                L.res_smem = need;
+                L.res_arrays = arrays;
+                break;
+            }
+        }
+        if (!L.resC)
+            return fail(BTE_EINVAL, "grid %dx%d does not fit the shared memory of a 16-CTA cluster",
+                        p->n_max + 1, p->m_points);
+    }
     L.G = (int)(128 / L.elem);
     L.H = (int)(32 / L.elem); /* halo columns the step kernel streams per side */
     const int max_tile = L.elem == 8 ? bte::step_max_tile<double>(L.vec)
@@ -236,6 +267,8 @@ int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L
     o += 256;
     L.off_fin = o;
     o += 256;
+    L.off_res = o;
+    o += kResBytes;
     L.total = o;
     return BTE_OK;
 }
@@ -467,12 +500,81 @@ int capture_graph(bte_handle* h, int set) {
     return BTE_OK;
 }
 
+/* On-chip mode: one persistent launch of the on-chip kernel (one cluster,
+ * one point) advances the current ping-pong set n steps in place, writing
+ * the per-step samples into the trace; the set does not change. */
+template <typename T>
+int enqueue_resident(bte_handle* h, long long n) {
+    const Layout& L = h->L;
+    const int set = h->set;
+    unsigned char* res = h->mem + L.off_res;
+    bte::BatchInst<T> R{};
+    static_assert(sizeof(R) <= 448, "record region");
+    for (int s = 0; s < 2; ++s) {
+        R.a_w[s] = h->ptr<T>(L.off_state[4 * set + 0]);
+        R.b_w[s] = h->ptr<T>(L.off_state[4 * set + 1]);
+        R.a_f[s] = h->ptr<T>(L.off_state[4 * set + 2]);
+        R.b_f[s] = h->ptr<T>(L.off_state[4 * set + 3]);
+    }
+    R.row_a0 = h->ptr<T>(L.off_row_a0);
+    R.col_g = h->ptr<T>(L.off_col_g);
+    R.col_phi = h->ptr<T>(L.off_col_phi);
+    R.e_whole = h->ptr<T>(L.off_ew);
+    R.e_frac = h->ptr<T>(L.off_ef);
+    R.part = h->ptr<double>(L.off_part);
+    R.ticket = h->ptr<unsigned>(L.off_ticket);
+    R.acc = reinterpret_cast<double*>(res + 512); /* window sums: scratch here */
+    R.K = n;
+    R.Kw = 0;
+    R.k0 = h->k;
+    R.trace_v = h->ptr<double>(L.off_tv);
+    R.trace_n = h->ptr<double>(L.off_tn);
+    R.N = h->p.n_max;
+    R.M = h->p.m_points - 1;
+    R.pitch = L.pitch;
+    R.P = h->tg.P > 0 ? (int)h->tg.P : 0;
+    R.dstride = (h->tg.P > 0 ? (int)h->tg.P : 1) + 2;
+    R.ntx = L.ntx;
+    R.nty = L.nty;
+    R.item0 = 0;
+    const double dt = h->tg.dt_eff;
+    R.h = (T)dt;
+    R.hh = (T)(0.5 * dt);
+    R.nu = (T)(1.0 + 0.5 * dt);
+    R.xi = (T)(1.0 - 0.5 * dt);
+    const double sq = std::sqrt(h->p.alpha);
+    R.vscale = kPi * sq * h->dphi;
+    R.nscale = 2.0 * kPi * sq * h->dphi;
+    R.omega = h->p.omega;
+    R.dt_eff = dt;
+    /* pageable source: staged before the call returns */
+    CU(cudaMemcpyAsync(res, &R, sizeof R, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemsetAsync(res + 448, 0, 64, h->stream)); /* order[0] = 0, queue = 0 */
+    bte::ResArgs<T> ra{};
+    ra.inst = reinterpret_cast<const bte::BatchInst<T>*>(res);
+    ra.order = reinterpret_cast<const int*>(res + 448);
+    ra.count = 1;
+    ra.queue = reinterpret_cast<unsigned*>(res + 452);
+    ra.C = L.resC;
+    ra.red_off = L.res_arrays;
+    /* the kernel's shared-memory attribute is per function: another handle or
+     * a batched run may have set it since this handle was created */
+    int clusters = 0;
+    int rc = bte::resident_max_clusters<T>(L.resC, L.res_smem, kResThreads, &clusters);
+    if (!rc) rc = bte::launch_resident<T>(ra, 1, kResThreads, L.res_smem, h->stream);
+    if (!rc) rc = bte::launch_advance_base(h->ptr<long long>(L.off_base), n, h->stream);
+    if (rc) return fail(BTE_ECUDA, "on-chip step kernel: %s", cudaGetErrorString((cudaError_t)rc));
+    h->k += n;
+    return BTE_OK;
+}
+
 /* Queues n steps: whole graphs of graph_len steps (one graph per starting
  * ping-pong set, captured on first use), then single launches.  Every launch
  * advances one step and flips the ping-pong set; launches after the first of
  * a run use programmatic dependent launch. */
 template <typename T>
 int enqueue_steps(bte_handle* h, long long n) {
+    if (h->L.resC) return n > 0 ? enqueue_resident<T>(h, n) : BTE_OK;
     while (h->graph_len >= 2 && n >= h->graph_len) {
         const int set = h->set;
         if (!h->graph[set]) {
@@ -789,7 +891,7 @@ int run_batch(const bte_params* p, std::vector<BatchPoint>& pts, size_t first, s
         /* the launch holding the longest point first */
         std::sort(launches.begin(), launches.end(),
                   [](const Launch& a, const Launch& b) { return a.longest > b.longest; });
-        constexpr int kThreads = 512;
+        constexpr int kThreads = kResThreads;
         cudaEvent_t ready = nullptr;
         BCU(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
         BCU(cudaEventRecord(ready, st));
@@ -1322,6 +1424,16 @@ int bte_create_ex(const bte_params* p, void* stream, const bte_tuning* tune, voi
         if (bps < 1) return bail(fail(BTE_EINVAL, "launch shape does not fit on an SM"));
         const long long slots = (long long)bps * sms;
         h->grid[1] = (int)(items < slots ? items : slots);
+    }
+    if (h->L.resC) {
+        /* sets the on-chip kernel's shared-memory (and cluster-size) attributes */
+        int clusters = 0;
+        rc = h->fp64 ? bte::resident_max_clusters<double>(h->L.resC, h->L.res_smem, kResThreads, &clusters)
+                     : bte::resident_max_clusters<float>(h->L.resC, h->L.res_smem, kResThreads, &clusters);
+        if (rc) return bail(fail(BTE_ECUDA, "on-chip kernel configure: %s", cudaGetErrorString((cudaError_t)rc)));
+        if (clusters < 1)
+            return bail(fail(BTE_EINVAL, "a cluster of %d CTAs with %zu bytes each cannot be scheduled",
+                             h->L.resC, h->L.res_smem));
     }
     rc = h->fp64 ? upload_tables<double>(h) : upload_tables<float>(h);
     if (rc) return bail(rc);

@@ -83,6 +83,9 @@ struct BatchInst {
                              max |norm-1|, non-finite flag, v and norm of the
                              latest step, v and norm of step 0               */
     long long K, Kw;      /* steps of the run, window samples                    */
+    long long k0;         /* step index of the state the run starts from (the
+                             on-chip kernel continues a single instance's run) */
+    double *trace_v, *trace_n; /* [k0 + K + 1] per-step samples, or NULL         */
     int N, M, pitch, P, ntx, nty;
     int dstride;
     int item0;            /* index of the instance's first work item            */

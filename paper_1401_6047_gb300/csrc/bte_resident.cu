@@ -19,6 +19,10 @@
  * by cost); there are no spin-waits: the only waits are cluster barriers,
  * which every CTA of a cluster passes the same number of times (all CTAs
  * run the same point for the same number of steps).
+ *
+ * The single-instance solver's on-chip mode launches the same kernel with
+ * one point: the run continues from step k0 of that instance (drive phase
+ * (k0 + k) mod P) and the per-step drift velocity and norm go to its trace.
  */
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
@@ -353,7 +357,7 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
          * step's last block barrier. */
         cluster_arrive(); /* initial state loaded */
         for (long long k = 0; k < K; ++k) {
-            const int kk = PP > 0 ? (int)(k % PP) : 0;
+            const int kk = PP > 0 ? (int)((I.k0 + k) % PP) : 0;
             const Half<T> Dw = half_drive<T>(I.e_whole, I.dstride, kk);
             const Half<T> Df = half_drive<T>(I.e_frac, I.dstride, kk);
             /* ---- whole grid: z_w^{k+1} = T(z_w^k; S(z_f^{k+1/2})) ---- */
@@ -408,6 +412,10 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                 if (!isfinite(vv) || !isfinite(nn)) acc[3] = 1.0;
                 acc[4] = vv;
                 acc[5] = nn;
+                if (I.trace_v) {
+                    I.trace_v[I.k0 + k1] = vv;
+                    I.trace_n[I.k0 + k1] = nn;
+                }
             }
         }
         cluster_wait(); /* pairs the last arrive */

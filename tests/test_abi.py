@@ -1,6 +1,7 @@
 """CPU-side checks of the C ABI library: it loads without a GPU, exports every
 symbol the headers declare, and its host-only helpers (Miller Bessel ratios,
 time grid, parameter validation) are right."""
+import ctypes
 import glob
 import math
 import os
@@ -69,6 +70,24 @@ def test_invalid_parameters_rejected_on_host(bad):
     with pytest.raises(bte.BteError) as e:
         bte.workspace_size(W.c1_fp64().replace(**bad))
     assert e.value.code == bte.EINVAL
+
+
+def test_on_chip_single_instance_mode_is_planned_on_host():
+    """resident=1 (one cluster holds the grid): a grid that fits plans with
+    the same device layout as the streamed mode; one that does not fit any
+    16-CTA cluster, or a bad flag, is rejected before any CUDA call."""
+    p = W.c1_fp64()
+    assert bte.workspace_size(p, resident=1) == bte.workspace_size(p)
+    with pytest.raises(bte.BteError) as e:
+        bte.workspace_size(W.c2(), resident=1)  # 401 x 4001: about 26 MB of state
+    assert e.value.code == bte.EINVAL
+    for bad in (dict(resident=2), dict(reserved=1)):
+        t = bte._tuning()
+        for k, v in bad.items():
+            setattr(t, k, v)
+        n = ctypes.c_size_t()
+        rc = bte.lib().bte_workspace_size(ctypes.byref(bte.to_params(p)), ctypes.byref(t), ctypes.byref(n))
+        assert rc == bte.EINVAL
 
 
 def test_workspace_size_covers_state():
