@@ -3,7 +3,8 @@
  * homogeneous superlattice Boltzmann transport equation
  *     df/dt + (E + B phi_y) df/dphi_x - B sin(phi_x) df/dphi_y = f0 - f
  * (Priimak, arXiv:1401.6047, Sec. 2, Eq. boltzmann_final), with the drive
- * E(t) = E_dc + E_omega cos(omega t) and a constant B.
+ * E(t) = E_dc + E_omega cos(omega t) and a constant B (the paper's runs) or
+ * B(t) = B + B_omega cos(omega t + B_phase) (bte_params.B_omega, B_phase).
  *
  * f is held as Fourier harmonics a_n(phi_y), b_n(phi_y), n = 0..n_max
  * (Sec. 2, Eq. f_fourier) on a uniform phi_y grid, and advanced by the
@@ -29,7 +30,9 @@
  *   coefficient B dt/(4 dphi) without alpha; b_0 = 0 (Eq. b_boundary);
  *   theta at the step start, theta' at its end; start-up half step with
  *   dt/2; dt adjusted to a whole number of steps per drive period; window
- *   averages over whole periods; observables from the whole grid.
+ *   averages over whole periods; observables from the whole grid; a
+ *   time-dependent B sampled where E is, and in the stencil coefficient at
+ *   the time of the grid that supplies the stencil.
  */
 #ifndef BTE_H
 #define BTE_H
