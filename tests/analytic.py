@@ -115,7 +115,7 @@ def f0_fourier(mu: float, alpha: float, nmax: int, phiy: np.ndarray, nx: int = 1
 def characteristics_ac(E_dc: float, E_omega: float, omega: float, B: float, mu: float,
                        nphase: int = 12, nx: int = 64, ny: int = 96, ds: float = 0.01,
                        smax: float = 25.0, ysig: float = 7.0, B_omega: float = 0.0,
-                       B_phase: float = 0.0):
+                       B_phase: float = 0.0, xsig: float = 0.0):
     """Periodic-state absorption and time-averaged drift velocity for the
     drive E(t) = E_dc + E_omega cos(omega t) and the field
     B(t) = B + B_omega cos(omega t + B_phase) (constant for B_omega = 0), by
@@ -129,11 +129,17 @@ def characteristics_ac(E_dc: float, E_omega: float, omega: float, B: float, mu: 
         <v>              = (1/T) int_0^T dtau int_0^inf du e^{-u} G(tau, u),
     G(tau, u) = < sin Phi_x(tau + u; tau, phi0) >_{f0}.  Midpoint rule in tau
     (periodic integrand), midpoint quadrature over phi0 (von Mises(mu) x
-    normal(0, 1/mu)), RK4 in u, Simpson in u.  Returns (A, v_dc) with
+    normal(0, 1/mu)), RK4 in u, Simpson in u.  At low temperature (large
+    mu) the start points can be confined to |phi_x| < xsig/sqrt(mu) (xsig > 0),
+    where the von Mises weight is not negligible.  Returns (A, v_dc) with
     A = (2 I_0/I_1) <v cos(omega t)> (Eq. absorption_def)."""
     T = 2 * np.pi / omega
     tau = T * (np.arange(nphase) + 0.5) / nphase
-    x = 2 * np.pi * (np.arange(nx) + 0.5) / nx - np.pi
+    if xsig > 0:
+        Lx = min(np.pi, xsig / np.sqrt(mu))
+        x = -Lx + 2 * Lx * (np.arange(nx) + 0.5) / nx
+    else:
+        x = 2 * np.pi * (np.arange(nx) + 0.5) / nx - np.pi
     wx = np.exp(mu * (np.cos(x) - 1.0))
     wx /= wx.sum()
     L = ysig / np.sqrt(mu)
