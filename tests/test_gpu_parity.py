@@ -78,6 +78,22 @@ def _rand_params(n_max, m_points, prec, omega=1.3):
                     avg_window=1.0, precision=prec)
 
 
+def test_low_temperature_fp64_matches_oracle():
+    """The paper's low-temperature point (mu = 116, B = 4, E_omega = 0.1,
+    E_dc = 6, alpha = 0.9496, omega = 3; 61 harmonics, 1201 phi_y points,
+    12 drive periods): the regime of high harmonics and a narrow f0, where
+    the oracle is pinned by the characteristics integral."""
+    p = W.Params(E_dc=6.0, E_omega=0.1, omega=3.0, B=4.0, mu=116.0, alpha=0.9496, n_max=60,
+                 m_points=1201, phiy_min=-6.0, phiy_max=6.0, dt=2e-3, periods=12.0,
+                 avg_window=1.0)
+    ref = oracle.solve(p)
+    o = bte.solve(p)
+    assert o.status == bte.OK
+    assert abs(o.absorption - ref.A) <= RTOL64 * abs(ref.A)
+    assert abs(o.v_dc_avg - ref.v_dc) <= RTOL64 * abs(ref.v_dc)
+    assert abs(o.norm_max_abs_err - ref.norm_err) <= 1e-13
+
+
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("prec,vec", [(W.FP64, 2), (W.FP32_MIXED, 2), (W.FP32_MIXED, 4)])
 def test_random_state_parity(shape, prec, vec):
