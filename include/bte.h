@@ -127,6 +127,15 @@ typedef struct {
                             one persistent launch that advances the state in
                             place (the kernel of the batched run's on-chip
                             tier); BTE_EINVAL when the grid does not fit.
+                            2: persistent -- the state stays in global
+                            memory (held in L2 across steps when it fits
+                            there) and each bte_step/bte_run call is one
+                            cooperative launch per 8192 steps whose CTAs
+                            (all resident at once) run the fused step for
+                            every step, with a grid barrier between steps
+                            (bounded by %globaltimer: BTE_ETIMEOUT when it
+                            gives up).  Same per-cell arithmetic and
+                            reduction order as mode 0: bit-identical.
                             0: one fused step kernel launch per step.      */
     int32_t reserved;    /* must be 0                                      */
 } bte_tuning;
@@ -167,6 +176,19 @@ BTE_API int bte_run(bte_handle* h);
  * an Inf or |norm - 1| > 0.05 was seen; BTE_ETIMEOUT after a bounded wait in
  * a kernel gave up). */
 BTE_API int bte_observables(bte_handle* h, bte_obs* out);
+
+/* Exercises the failure detection of the bounded in-kernel waits without a
+ * fault (the paper has no counterpart; failure handling is the library's
+ * own).  Queues one kernel whose single thread waits on a shared-memory
+ * mbarrier that nothing completes, bounded by limit_ns nanoseconds of the
+ * GPU's %globaltimer (1 <= limit_ns <= 2e9; the solver kernels' own waits
+ * give up after 2e9), and then records the timeout in the handle's error
+ * word exactly as a solver kernel whose wait gave up does: bte_observables
+ * returns BTE_ETIMEOUT (status BTE_ETIMEOUT) until bte_reset clears the
+ * word.  No copy or other asynchronous work is in flight when the wait
+ * gives up, and the context stays usable.  BTE_EINVAL for a NULL handle or
+ * a limit out of range. */
+BTE_API int bte_wait_probe(bte_handle* h, int64_t limit_ns);
 
 /* Copies whole-grid samples k0..k0+count-1 of v_dr and norm (HOST arrays,
  * either may be NULL).  Samples beyond the current step are BTE_EINVAL. */
@@ -232,7 +254,11 @@ BTE_API int bte_launch_shape(const bte_params* p, const bte_tuning* tune, int32_
  * may be at most 1,048,576 (BTE_EINVAL beyond that, below 3, or for bad
  * parameters).  Its first call on a device looks up that array's device
  * address (cudaGetSymbolAddress, with the device current); make that first
- * call before any stream capture.  Every call shares the array and clears
+ * call before any stream capture.  Later calls outside capture look the
+ * address up again (a device reset by the caller moves the array); calls
+ * while `stream` is capturing reuse the address found by the device's last
+ * call outside capture, so after a cudaDeviceReset make one call outside
+ * capture before capturing again.  Every call shares the array and clears
  * the ticket before use; calls that overlap on the GPU race. */
 BTE_API int bte_observe_noalloc(const bte_params* p, const void* a0_row, const void* b1_row,
                                 double* out, void* stream);

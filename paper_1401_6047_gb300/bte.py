@@ -102,6 +102,7 @@ def lib() -> ctypes.CDLL:
                                ctypes.POINTER(i64)], ctypes.c_int),
             "bte_version": ([], ctypes.c_char_p),
             "bte_observe_noalloc": ([P, vp, vp, vp, vp], ctypes.c_int),
+            "bte_wait_probe": ([vp, i64], ctypes.c_int),
             "bte_launch_shape": ([P, T] + [ctypes.POINTER(ctypes.c_int32)] * 5, ctypes.c_int),
             "bte_batch_run": ([P, ctypes.c_int32, ctypes.POINTER(bte_obs),
                                ctypes.POINTER(bte_batch_opts)], ctypes.c_int),
@@ -296,6 +297,12 @@ class Solver:
         out = np.zeros((int(nphix), self.shape[1]))
         _check(self._lib.bte_pdf(self._h, int(grid), int(nphix), _dp(out)))
         return out
+
+    def wait_probe(self, limit_ns: int) -> None:
+        """Queues ``bte_wait_probe``: one bounded in-kernel wait that nothing
+        completes, recorded in the error word as a solver timeout (the next
+        ``observables`` call reports ``ETIMEOUT`` until ``reset``)."""
+        _check(self._lib.bte_wait_probe(self._h, int(limit_ns)))
 
     def set_step(self, k: int, v: np.ndarray, norm: np.ndarray) -> None:
         v = np.ascontiguousarray(v, dtype=np.float64)

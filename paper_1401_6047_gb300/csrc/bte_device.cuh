@@ -51,12 +51,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-/* Bounded wait on an mbarrier phase: false after ~2 s of %globaltimer. */
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+/* Default limit of a bounded wait: 2 s of %globaltimer. */
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+/* Bounded wait on an mbarrier phase: false once limit_ns of %globaltimer
+ * have passed without the phase completing. */
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          uint64_t limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer();
     while (!mbar_try_wait(bar, parity)) {
-        if (global_timer() - t0 > 2000000000ull) return false;
+        if (global_timer() - t0 > limit_ns) return false;
     }
     return true;
 }
@@ -93,16 +98,56 @@ __device__ __forceinline__ double recip<double>(double x) {
     return 1.0 / x;
 }
 
-/* a * b + c with one rounding. */
+/* Arithmetic with exactly one rounding per operation and no contraction
+ * left to the compiler (the _rn intrinsics are never fused or reordered).
+ * Every kernel that applies the per-cell update -- streamed, persistent,
+ * on-chip, start-up -- goes through these, so they all perform the same
+ * sequence of roundings and agree bit for bit. */
 template <typename T>
-__device__ __forceinline__ T fma_t(T a, T b, T c);
+struct Rn;
 template <>
-__device__ __forceinline__ float fma_t<float>(float a, float b, float c) {
-    return fmaf(a, b, c);
+struct Rn<float> {
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+};
+template <>
+struct Rn<double> {
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+};
+
+/* Constants of the Crank-Nicolson operator T_h (Sec. 3): nu = 1 + h/2,
+ * xi = 1 - h/2 and the products nu^2, nu h. */
+template <typename T>
+struct CnK {
+    T h, nu, xi, nu2, nuh;
+};
+template <typename T>
+__device__ __forceinline__ CnK<T> cn_constants(T h, T nu, T xi) {
+    return CnK<T>{h, nu, xi, Rn<T>::mul(nu, nu), Rn<T>::mul(nu, h)};
 }
-template <>
-__device__ __forceinline__ double fma_t<double>(double a, double b, double c) {
-    return fma(a, b, c);
+
+/* Rotation factor (E + B phi_y) h/2 of one column at one time (the theta of
+ * Eqs. a_t_plus_1, b_t_plus_1 is n times it). */
+template <typename T>
+__device__ __forceinline__ T rot_factor(T E, T B, T phi, T hh) {
+    return Rn<T>::mul(Rn<T>::fma(B, phi, E), hh);
+}
+
+/* The paper's stencil terms from central differences D x_r(m) of the other
+ * grid: B^t = c (D b_{n+1} - D b_{n-1}) acts on a, A^t = c (chi(n) D a_{n-1}
+ * - D a_{n+1}) on b (chi(1) = 2: the n = 1 row reads a_0 twice, Sec. 3). */
+template <typename T>
+__device__ __forceinline__ T stencil_a(T c, T db_next, T db_prev) {
+    return Rn<T>::mul(c, Rn<T>::sub(db_next, db_prev));
+}
+template <typename T>
+__device__ __forceinline__ T stencil_b(T c, T chi, T da_prev, T da_next) {
+    return Rn<T>::mul(c, Rn<T>::fma(chi, da_prev, -da_next));
 }
 
 /* Crank-Nicolson update of one cell (Sec. 3, Eqs. a_t_plus_1, b_t_plus_1,
@@ -113,20 +158,86 @@ __device__ __forceinline__ double fma_t<double>(double a, double b, double c) {
  *   db = [th1 (Sa + h a0) + nu Sb + a (th nu + xi th1) - b (nu h + th1 (th + th1))] / D
  * which equals a' - a, b' - b for a' = (g nu - q th1)/D, b' = (g th1 + q nu)/D,
  * g = a xi - b th + Sa + h a0, q = b xi + a th + Sb.  Sa is the paper's B^t
- * stencil term (acts on a), Sb its A^t term (acts on b). */
+ * stencil term (acts on a), Sb its A^t term (acts on b); h a0 = hr g with
+ * hr = h times the row factor and g the column factor of the separable
+ * equilibrium.  Each product, sum and fused multiply-add below is one
+ * rounding, in this order. */
 template <typename T>
-__device__ __forceinline__ void cn_cell(T a, T b, T Sa, T Sb, T ha0, T th, T th1, T nu, T xi,
-                                        T h, T& an, T& bn) {
-    const T D = nu * nu + th1 * th1;
+__device__ __forceinline__ void cn_cell(T a, T b, T Sa, T Sb, T hr, T g, T th, T th1,
+                                        const CnK<T>& k, T& an, T& bn) {
+    using O = Rn<T>;
+    const T D = O::fma(th1, th1, k.nu2);
     const T inv = recip<T>(D);
-    const T src = Sa + ha0;
-    const T ca = nu * h + th1 * (th + th1);
-    const T cb = th * nu + xi * th1;
-    const T da = (nu * src - th1 * Sb - a * ca - b * cb) * inv;
-    const T db = (th1 * src + nu * Sb + a * cb - b * ca) * inv;
-    an = a + da;
-    bn = b + db;
+    const T src = O::fma(hr, g, Sa);
+    const T ca = O::fma(th1, O::add(th, th1), k.nuh);
+    const T cb = O::fma(k.xi, th1, O::mul(th, k.nu));
+    T t = O::fma(k.nu, src, -O::mul(th1, Sb));
+    t = O::fma(-a, ca, t);
+    t = O::fma(-b, cb, t);
+    T u = O::fma(th1, src, O::mul(k.nu, Sb));
+    u = O::fma(a, cb, u);
+    u = O::fma(-b, ca, u);
+    an = O::add(a, O::mul(t, inv));
+    bn = O::add(b, O::mul(u, inv));
 }
+
+/* The update of V consecutive columns of one row (V = 2 or 4): the stencil
+ * terms from the other grid's differences in rows n+1 (next) and n-1 (prev),
+ * the rotations n w0, n w1 (w = rot_factor at the half-step's start and end)
+ * and cn_cell.  FP32 runs two columns per instruction with Blackwell's paired
+ * FP32 operations (__ffma2_rn, __fadd2_rn, __fmul2_rn), which round each
+ * component exactly as the scalar _rn form: the same bits as cn_cell on
+ * each column, in half the issue slots.  FP64 runs cn_cell per column. */
+__device__ __forceinline__ float2 pair(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+
+template <typename T, int V>
+__device__ __forceinline__ void cn_row(const T (&a)[V], const T (&b)[V], const T (&db_next)[V],
+                                       const T (&db_prev)[V], const T (&da_prev)[V],
+                                       const T (&da_next)[V], T cc, T chi, T hr, const T (&g)[V],
+                                       T nf, const T (&w0)[V], const T (&w1)[V], const CnK<T>& k,
+                                       T (&an)[V], T (&bn)[V]) {
+    if constexpr (sizeof(T) == 4 && V % 2 == 0) {
+        const float2 cc2 = pair(cc, cc), chi2 = pair(chi, chi), hr2 = pair(hr, hr);
+        const float2 nf2 = pair(nf, nf), nu2 = pair(k.nu2, k.nu2), nuh2 = pair(k.nuh, k.nuh);
+        const float2 nu = pair(k.nu, k.nu), xi = pair(k.xi, k.xi);
+#pragma unroll
+        for (int e = 0; e < V; e += 2) {
+            const float2 A = pair(a[e], a[e + 1]), Bv = pair(b[e], b[e + 1]);
+            const float2 Sa = __fmul2_rn(cc2, __fadd2_rn(pair(db_next[e], db_next[e + 1]),
+                                                         neg2(pair(db_prev[e], db_prev[e + 1]))));
+            const float2 Sb = __fmul2_rn(cc2, __ffma2_rn(chi2, pair(da_prev[e], da_prev[e + 1]),
+                                                         neg2(pair(da_next[e], da_next[e + 1]))));
+            const float2 th = __fmul2_rn(nf2, pair(w0[e], w0[e + 1]));
+            const float2 th1 = __fmul2_rn(nf2, pair(w1[e], w1[e + 1]));
+            const float2 D = __ffma2_rn(th1, th1, nu2);
+            const float2 inv = pair(recip<float>(D.x), recip<float>(D.y));
+            const float2 src = __ffma2_rn(hr2, pair(g[e], g[e + 1]), Sa);
+            const float2 ca = __ffma2_rn(th1, __fadd2_rn(th, th1), nuh2);
+            const float2 cb = __ffma2_rn(xi, th1, __fmul2_rn(th, nu));
+            float2 t = __ffma2_rn(nu, src, neg2(__fmul2_rn(th1, Sb)));
+            t = __ffma2_rn(neg2(A), ca, t);
+            t = __ffma2_rn(neg2(Bv), cb, t);
+            float2 u = __ffma2_rn(th1, src, __fmul2_rn(nu, Sb));
+            u = __ffma2_rn(A, cb, u);
+            u = __ffma2_rn(neg2(Bv), ca, u);
+            const float2 na = __fadd2_rn(A, __fmul2_rn(t, inv));
+            const float2 nb = __fadd2_rn(Bv, __fmul2_rn(u, inv));
+            an[e] = na.x;
+            an[e + 1] = na.y;
+            bn[e] = nb.x;
+            bn[e + 1] = nb.y;
+        }
+    } else {
+        using O = Rn<T>;
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+            cn_cell<T>(a[e], b[e], stencil_a<T>(cc, db_next[e], db_prev[e]),
+                       stencil_b<T>(cc, chi, da_prev[e], da_next[e]), hr, g[e],
+                       O::mul(nf, w0[e]), O::mul(nf, w1[e]), k, an[e], bn[e]);
+    }
+}
+
 
 /* Sum over the block in a fixed order (warp shuffles, then warp partials
  * in warp order); the result is valid in thread 0.  `red` holds >= 32

@@ -178,12 +178,18 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Layout {
     int G, H, pitch, tile_m, chunk_n, vec, ts, ntx, nty;
     int resC;                 /* on-chip mode: CTAs of the cluster, 0 = streamed */
+    bool persist;             /* persistent mode: one launch per call, grid barriers */
     size_t res_smem, res_arrays; /* its shared memory per CTA, and the arrays' part */
     size_t elem;
     size_t off_state[8];
     size_t off_row_a0, off_col_g, off_col_phi, off_ew, off_ef, off_tv, off_tn, off_part,
-        off_ticket, off_err, off_base, off_fin, off_res, total;
+        off_ticket, off_err, off_base, off_fin, off_res, off_done, total;
+    int dring;                /* slots of the row-0 partial sums (persistent: ntx + 1) */
 };
+
+/* steps of one persistent launch at most (a bte_step/bte_run call of more
+ * steps queues several launches) */
+constexpr long long kPersistMaxSteps = 8192;
 
 /* bytes of the on-chip mode's device record: the point's BatchInst, its
  * order entry and queue counter, and the kernel's window-sum scratch */
@@ -192,14 +198,16 @@ constexpr int kResThreads = 512; /* threads per CTA of the on-chip kernel */
 
 int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L) {
     if (t && t->reserved) return fail(BTE_EINVAL, "tuning.reserved must be 0");
-    if (t && (t->resident < 0 || t->resident > 1)) return fail(BTE_EINVAL, "tuning.resident must be 0 or 1");
+    if (t && (t->resident < 0 || t->resident > 2))
+        return fail(BTE_EINVAL, "tuning.resident must be 0, 1 or 2");
     int rc = pick_tile(p, t, L.tile_m, L.chunk_n, L.vec);
     if (rc) return rc;
     L.elem = p->precision == BTE_FP64 ? 8 : 4;
     /* on-chip mode: the largest cluster that leaves every CTA two rows and fits */
     L.resC = 0;
     L.res_smem = L.res_arrays = 0;
-    if (t && t->resident) {
+    L.persist = t && t->resident == 2;
+    if (t && t->resident == 1) {
         const int N1 = p->n_max + 1;
         for (int C = 16; C >= 1; C /= 2) {
             if (C > 1 && (N1 + C - 1) / C < 2) continue;
@@ -257,10 +265,13 @@ int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L
     o += align_up((size_t)(tg.K + 1) * 8, 256);
     L.off_tn = o;
     o += align_up((size_t)(tg.K + 1) * 8, 256);
+    /* a persistent launch may have steps k .. k + ntx in flight at once (an
+     * item's dependencies spread by one tile per step): that many slots */
+    L.dring = L.persist ? L.ntx + 1 : 1;
     L.off_part = o;
-    o += align_up((size_t)2 * L.ts * L.ntx * 8, 256);
+    o += align_up((size_t)2 * L.dring * L.ntx * 8, 256);
     L.off_ticket = o;
-    o += 256;
+    o += align_up((size_t)L.dring * sizeof(unsigned), 256);
     L.off_err = o;
     o += 256;
     L.off_base = o;
@@ -269,6 +280,8 @@ int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L
     o += 256;
     L.off_res = o;
     o += kResBytes;
+    L.off_done = o;
+    o += align_up((size_t)L.ntx * L.nty * sizeof(unsigned), 256);
     L.total = o;
     return BTE_OK;
 }
@@ -289,6 +302,7 @@ struct bte_handle {
     long long base_host;
     int graph_len; /* steps per captured graph (a multiple of the fused step count) */
     int grid[3];   /* persistent CTAs of the step kernel fusing 1 / 2 steps */
+    int grid_persist; /* CTAs of a persistent (multi-step) launch, all co-resident */
     int set;       /* ping-pong set holding the current state (flips per launch) */
     cudaGraphExec_t graph[2]; /* one graph per starting set */
     double r1;     /* I_1/I_0 */
@@ -322,6 +336,9 @@ bte::StepArgs<T> step_args(const bte_handle* h) {
     a.part = h->ptr<double>(L.off_part);
     a.ticket = h->ptr<unsigned>(L.off_ticket);
     a.err = h->ptr<int>(L.off_err);
+    a.done = h->ptr<unsigned>(L.off_done);
+    a.dring = L.dring;
+    a.nsteps = 0;
     a.N = h->p.n_max;
     a.M = h->p.m_points - 1;
     a.pitch = L.pitch;
@@ -572,9 +589,32 @@ int enqueue_resident(bte_handle* h, long long n) {
  * ping-pong set, captured on first use), then single launches.  Every launch
  * advances one step and flips the ping-pong set; launches after the first of
  * a run use programmatic dependent launch. */
+/* Persistent mode: launches of at most kPersistMaxSteps steps, each one
+ * cooperative launch of one CTA per work item that advances every step,
+ * an item starting a step once its neighbours have finished the step
+ * before (their completion counters zeroed before the launch). */
+template <typename T>
+int enqueue_persist(bte_handle* h, long long n) {
+    bte::StepArgs<T> a = step_args<T>(h);
+    a.grid = h->grid_persist;
+    while (n > 0) {
+        const long long c = n < kPersistMaxSteps ? n : kPersistMaxSteps;
+        a.nsteps = (int)c;
+        CU(cudaMemsetAsync(a.done, 0, (size_t)h->L.ntx * h->L.nty * sizeof(unsigned), h->stream));
+        int rc = bte::launch_step_persist<T>(a, h->set, h->stream);
+        if (!rc) rc = bte::launch_advance_base(h->ptr<long long>(h->L.off_base), c, h->stream);
+        if (rc) return fail(BTE_ECUDA, "persistent step kernel: %s", cudaGetErrorString((cudaError_t)rc));
+        h->k += c;
+        h->set ^= (int)(c & 1);
+        n -= c;
+    }
+    return BTE_OK;
+}
+
 template <typename T>
 int enqueue_steps(bte_handle* h, long long n) {
     if (h->L.resC) return n > 0 ? enqueue_resident<T>(h, n) : BTE_OK;
+    if (h->L.persist) return enqueue_persist<T>(h, n);
     while (h->graph_len >= 2 && n >= h->graph_len) {
         const int set = h->set;
         if (!h->graph[set]) {
@@ -1424,6 +1464,23 @@ int bte_create_ex(const bte_params* p, void* stream, const bte_tuning* tune, voi
         if (bps < 1) return bail(fail(BTE_EINVAL, "launch shape does not fit on an SM"));
         const long long slots = (long long)bps * sms;
         h->grid[1] = (int)(items < slots ? items : slots);
+        h->grid_persist = 0;
+        if (h->L.persist) {
+            int pb = 0;
+            rc = h->fp64 ? bte::step_kernel_configure_persist<double>(h->L.tile_m, h->L.chunk_n, h->L.vec, &pb)
+                         : bte::step_kernel_configure_persist<float>(h->L.tile_m, h->L.chunk_n, h->L.vec, &pb);
+            if (rc)
+                return bail(fail(BTE_ECUDA, "kernel configure: %s", cudaGetErrorString((cudaError_t)rc)));
+            if (pb < 1) return bail(fail(BTE_EINVAL, "launch shape does not fit on an SM"));
+            /* one CTA per item, every CTA co-resident */
+            const long long cap = (long long)pb * sms;
+            if (items > cap)
+                return bail(fail(BTE_EINVAL,
+                                 "persistent mode: %lld work items but %lld co-resident CTAs; "
+                                 "use larger chunk_n or tile_m",
+                                 items, cap));
+            h->grid_persist = (int)items;
+        }
     }
     if (h->L.resC) {
         /* sets the on-chip kernel's shared-memory (and cluster-size) attributes */
@@ -1506,10 +1563,20 @@ int bte_observables(bte_handle* h, bte_obs* out) {
     else if (fin[3] != 0.0 || !(fin[2] <= 0.05)) st = BTE_EUNSTABLE;
     out->status = st;
     out->reserved = 0;
-    if (st == BTE_ETIMEOUT) return fail(st, "a bounded wait in the step kernel gave up");
+    if (st == BTE_ETIMEOUT) return fail(st, "a bounded wait in a solver kernel gave up");
     if (st == BTE_EUNSTABLE)
         return fail(st, "unstable run: |norm-1| reached %g%s", fin[2],
                     fin[3] != 0.0 ? " (non-finite values)" : "");
+    return BTE_OK;
+}
+
+int bte_wait_probe(bte_handle* h, int64_t limit_ns) {
+    if (!h) return fail(BTE_EINVAL, "handle is NULL");
+    if (limit_ns < 1 || limit_ns > 2000000000ll)
+        return fail(BTE_EINVAL, "limit_ns %lld outside 1..2e9", (long long)limit_ns);
+    const int rc = bte::launch_wait_probe(h->ptr<int>(h->L.off_err), (unsigned long long)limit_ns,
+                                          h->stream);
+    if (rc) return fail(BTE_ECUDA, "wait probe kernel: %s", cudaGetErrorString((cudaError_t)rc));
     return BTE_OK;
 }
 

@@ -50,9 +50,13 @@ struct StepArgs {
     const long long* base;/* device step counter: the launch advances step base+i */
     double* trace_v;      /* [K+1] whole-grid v_dr samples                       */
     double* trace_n;      /* [K+1] whole-grid norm samples                       */
-    double* part;         /* [ts][2][ntx] per-tile partial sums of row 0 / row 1 */
-    unsigned* ticket;     /* arrival counter of the row-0 CTAs                   */
+    double* part;         /* [dring][2][ntx] per-tile partial sums of row 0 / row 1 */
+    unsigned* ticket;     /* [dring] arrival counters of the row-0 CTAs          */
+    int dring;            /* slots of part / ticket: step k uses slot k % dring  */
     int* err;             /* device error word (timeouts)                        */
+    unsigned* done;       /* [ntx * nty] steps each item has completed in a
+                             persistent launch (zero at its start)             */
+    int nsteps;           /* steps of a persistent launch                        */
     int N, M, pitch, P;
     int dstride;          /* row stride of the drive tables (>= P + 2)          */
     int tile_m, chunk_n, ntx, nty;
@@ -152,6 +156,17 @@ int launch_apply(const ApplyArgs<T>& a, void* stream);
  * overlaps the previous launch). */
 template <typename T>
 int launch_step(const StepArgs<T>& a, int i, int parity, bool pdl, void* stream);
+/* Persistent form: one cooperative launch of a.grid = ntx * nty CTAs, one
+ * work item each, advances a.nsteps steps from base (set `parity` holds
+ * step base).  Before step s > 0 an item waits until the items around it
+ * (its tile and chunk neighbours, whose step s - 1 output it reads and whose
+ * step s - 1 input it overwrites) have completed s steps in a.done (zeroed
+ * by the caller before the launch); a.dring > ntx slots of the row-0
+ * partial sums keep the steps that may be in flight at once apart. */
+template <typename T>
+int launch_step_persist(const StepArgs<T>& a, int parity, void* stream);
+template <typename T>
+int step_kernel_configure_persist(int tile_m, int chunk_n, int vec, int* blocks_per_sm);
 /* Batched form: every active instance of the batch advances one step. */
 template <typename T>
 int launch_step_batch(const BatchArgs<T>& a, int i, int parity, bool pdl, void* stream);
@@ -162,6 +177,8 @@ int launch_observe(const T* a_w, const T* b_w, int M, int pitch, double vscale,
                    double nscale, double* trace_v, double* trace_n, long long slot,
                    void* stream);
 int launch_advance_base(long long* base, long long by, void* stream);
+/* one bounded wait that nothing completes; records kErrTimeout in *err */
+int launch_wait_probe(int* err, unsigned long long limit_ns, void* stream);
 int launch_finalize(const FinalArgs& a, void* stream);
 /* f on an nphix x (M+1) grid from the harmonics of one grid: out [nphix][M+1] (device) */
 template <typename T>

@@ -45,22 +45,24 @@ __global__ void apply_kernel(ApplyArgs<T> A) {
     const int n = blockIdx.y;
     if (m > A.M || n > A.N) return;
     const int c = G + m;
+    using O = Rn<T>;
     const T chi = (n == 1) ? (T)2 : (T)1;
     const T ph = A.col_phi[c];
-    const T th = (T)n * (((T)A.E_start + (T)A.B_start * ph) * A.hh);
-    const T th1 = (T)n * (((T)A.E_end + (T)A.B_end * ph) * A.hh);
+    const T nf = (T)n;
+    const T th = O::mul(nf, rot_factor<T>((T)A.E_start, (T)A.B_start, ph, A.hh));
+    const T th1 = O::mul(nf, rot_factor<T>((T)A.E_end, (T)A.B_end, ph, A.hh));
     const int N = A.N, P = A.pitch;
     const T bu = ld_or0(A.bs, n + 1, c + 1, N, P) - ld_or0(A.bs, n + 1, c - 1, N, P);
     const T bd = (n - 1 >= 1) ? ld_or0(A.bs, n - 1, c + 1, N, P) - ld_or0(A.bs, n - 1, c - 1, N, P)
                               : (T)0;
     const T ad = ld_or0(A.as, n - 1, c + 1, N, P) - ld_or0(A.as, n - 1, c - 1, N, P);
     const T au = ld_or0(A.as, n + 1, c + 1, N, P) - ld_or0(A.as, n + 1, c - 1, N, P);
-    const T Sa = A.c * (bu - bd);
-    const T Sb = A.c * (chi * ad - au);
+    const T Sa = stencil_a<T>(A.c, bu, bd);
+    const T Sb = stencil_b<T>(A.c, chi, ad, au);
     const size_t g = (size_t)n * P + c;
     T an, bn;
-    cn_cell<T>(A.a[g], A.b[g], Sa, Sb, A.h * A.row_a0[n] * A.col_g[c], th, th1, A.nu, A.xi, A.h,
-               an, bn);
+    cn_cell<T>(A.a[g], A.b[g], Sa, Sb, O::mul(A.h, A.row_a0[n]), A.col_g[c], th, th1,
+               cn_constants<T>(A.h, A.nu, A.xi), an, bn);
     if (n == 0) bn = (T)0;
     A.an[g] = an;
     A.bn[g] = bn;
@@ -156,6 +158,20 @@ __global__ void pdf_kernel(const T* a, const T* b, int N, int M, int pitch, int 
     out[(size_t)i * (M + 1) + m] = f;
 }
 
+/* The failure-detection path of the bounded waits, exercised without a
+ * fault: one thread waits on a fresh mbarrier that no thread arrives on and
+ * no copy completes, for limit_ns of %globaltimer, then records the timeout
+ * in the error word as the solver kernels do.  Nothing is in flight when it
+ * returns. */
+__global__ void wait_probe_kernel(int* err, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = smem_u32(&bar);
+    mbar_init(b, 1);
+    if (!mbar_wait(b, 0u, limit_ns)) atomicExch(err, kErrTimeout);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(b) : "memory");
+}
+
 }  // namespace
 
 /* ---------------------------------------------------------------------- */
@@ -188,6 +204,11 @@ int launch_observe(const T* a_w, const T* b_w, int M, int pitch, double vscale, 
 
 int launch_advance_base(long long* base, long long by, void* stream) {
     advance_base_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(base, by);
+    return ok_or(cudaGetLastError());
+}
+
+int launch_wait_probe(int* err, unsigned long long limit_ns, void* stream) {
+    wait_probe_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(err, limit_ns);
     return ok_or(cudaGetLastError());
 }
 

@@ -15,8 +15,12 @@
  * g_noalloc_scratch is a __device__ array: every GPU that loads this library
  * holds its kNoAllocScratchBytes until the process exits.  Host code must
  * not pass the array's name to a kernel (on the host it is only a stand-in);
- * its device address is looked up once per device with
- * cudaGetSymbolAddress and passed to the kernel.
+ * its device address comes from cudaGetSymbolAddress, with the device
+ * current, and is passed to the kernel.  The first call on a device does
+ * that look-up; later calls outside stream capture repeat it (a cheap
+ * runtime query, and the address changes when the caller resets the
+ * device, which reloads the library's module), and calls during capture use
+ * the address of the device's last call outside capture.
  */
 #include <cuda_runtime.h>
 
@@ -81,13 +85,16 @@ __global__ void observe_noalloc_kernel(const T* a0, const T* b1, int m_points, d
     }
 }
 
-/* Device address of g_noalloc_scratch on the current device, looked up on
- * the first call for that device (with the device current). */
-int scratch_address(unsigned char** ptr) {
+/* Device address of g_noalloc_scratch on the current device: looked up
+ * with the device current on every call outside stream capture (and cached
+ * per device), taken from that cache while `s` is capturing. */
+int scratch_address(cudaStream_t s, unsigned char** ptr) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BTE_ECUDA;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return BTE_ECUDA;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone || !g_scratch_addr[dev]) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return BTE_ECUDA;
@@ -107,10 +114,10 @@ extern "C" int bte_observe_noalloc(const bte_params* p, const void* a0_row, cons
         !std::isfinite(p->phiy_min) || !std::isfinite(p->phiy_max))
         return BTE_EINVAL;
     if (p->precision != BTE_FP64 && p->precision != BTE_FP32_MIXED) return BTE_EINVAL;
-    unsigned char* scratch = nullptr;
-    int rc = scratch_address(&scratch);
-    if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned char* scratch = nullptr;
+    int rc = scratch_address(s, &scratch);
+    if (rc) return rc;
     /* the ticket must start at zero; a call that ended early may have left it set */
     if (cudaMemsetAsync(scratch + kTicketOffset, 0, sizeof(unsigned), s) != cudaSuccess)
         return BTE_ECUDA;

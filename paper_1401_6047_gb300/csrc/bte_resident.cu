@@ -36,6 +36,11 @@ namespace bte {
 namespace {
 
 using dev::cn_cell;
+using dev::CnK;
+using dev::Rn;
+using dev::rot_factor;
+using dev::stencil_a;
+using dev::stencil_b;
 
 template <typename T>
 struct RV {
@@ -120,30 +125,28 @@ __device__ __forceinline__ Half<T> half_drive(const T* tab, int stride, int kk) 
 /* One half-step (Sec. 3, Eqs. a_t_plus_1, b_t_plus_1, in increment form) on
  * the V cells of a group at harmonic n, in place: oA, oB the own grid's a, b;
  * da_u, da_d, db_u, db_d the phi_y differences of the other grid's a and b
- * in rows n-1 (u) and n+1 (d); t0, t1 the drive/field factors
- * (E + B phi_m) dt/4 at the start and end of the half-step.  Same
- * expressions as the streaming kernel. */
+ * in rows n-1 (u) and n+1 (d); t0, t1 the rotation factors
+ * (E + B phi_m) dt/2 at the start and end of the half-step.  The same
+ * operations in the same order as the streaming kernel (cn_row), so the
+ * two give the same bits per cell. */
 template <typename T>
 __device__ __forceinline__ void cell_group(T* oA, T* oB, const T (&da_u)[RV<T>::V],
                                            const T (&da_d)[RV<T>::V], const T (&db_u)[RV<T>::V],
-                                           const T (&db_d)[RV<T>::V], int n, int m0, int M, T ha0,
+                                           const T (&db_d)[RV<T>::V], int n, int m0, int M, T hr,
                                            const T (&gc)[RV<T>::V], const T (&t0)[RV<T>::V],
-                                           const T (&t1)[RV<T>::V], T nu, T xi, T h, T cc,
+                                           const T (&t1)[RV<T>::V], const CnK<T>& K, T cc,
                                            bool on) {
     constexpr int V = RV<T>::V;
-    T oa[V], ob[V], na[V], nb[V];
+    T oa[V], ob[V], an[V], bn[V], na[V], nb[V];
     ld_vec<T>(oA, oa);
     ld_vec<T>(oB, ob);
-    const T nf = (T)n;
     const T chi = (n == 1) ? (T)2 : (T)1;
+    dev::cn_row<T, V>(oa, ob, db_d, db_u, da_u, da_d, cc, chi, hr, gc, (T)n, t0, t1, K, an, bn);
 #pragma unroll
     for (int e = 0; e < V; ++e) {
-        T an, bn;
-        cn_cell<T>(oa[e], ob[e], cc * (db_d[e] - db_u[e]), cc * (chi * da_u[e] - da_d[e]),
-                   ha0 * gc[e], nf * t0[e], nf * t1[e], nu, xi, h, an, bn);
         const bool ok = m0 + e <= M;
-        na[e] = ok ? an : (T)0;
-        nb[e] = (ok && n > 0) ? bn : (T)0;
+        na[e] = ok ? an[e] : (T)0;
+        nb[e] = (ok && n > 0) ? bn[e] : (T)0;
     }
     if (!on) return;
     st_vec<T>(oA, na);
@@ -196,7 +199,8 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
         const int r0 = min(N1, rank * rows_per), r1 = min(N1, r0 + rows_per), R = r1 - r0;
         const int ncg = (M + 1 + V - 1) / V;
         const long long K = I.K, Kw = I.Kw;
-        const T h = I.h, hh = I.hh, nu = I.nu, xi = I.xi;
+        const T h = I.h, hh = I.hh;
+        const CnK<T> cn = dev::cn_constants<T>(h, I.nu, I.xi);
         /* shared-memory layout of this point: 4 arrays of rows_per + 2 rows
          * (halo, own rows, halo) with row stride P = ghost + columns + ghost */
         const int P = LG + ncg * V + V;
@@ -284,8 +288,8 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                 for (int e = 0; e < V; ++e) {
                     const T ph = sPh[LG + m0 + e];
                     gc[e] = sG[LG + m0 + e];
-                    t0[e] = (D.E0 + D.B0 * ph) * hh;
-                    t1[e] = (D.E1 + D.B1 * ph) * hh;
+                    t0[e] = rot_factor<T>(D.E0, D.B0, ph, hh);
+                    t1[e] = rot_factor<T>(D.E1, D.B1, ph, hh);
                 }
                 const T* xa = sAw + x * arr + LG + m0; /* other grid, shared row 0 */
                 for (int ch = 0; ch < 2; ++ch) {
@@ -309,8 +313,8 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                         diff_sh<T>(xa + arr + (size_t)(il + 2) * P, l_adj, r_adj, db_d);
                         const size_t c = (size_t)(il + 1) * P + LG + m0;
                         cell_group<T>(sAw + o * arr + c, sAw + (o + 1) * arr + c, da_u, da_d, db_u,
-                                      db_d, r0 + il, m0, M, h * sR[il + 1], gc, t0, t1, nu, xi, h,
-                                      D.cc, on);
+                                      db_d, r0 + il, m0, M, Rn<T>::mul(h, sR[il + 1]), gc, t0, t1,
+                                      cn, D.cc, on);
 #pragma unroll
                         for (int e = 0; e < V; ++e) {
                             da_u[e] = da_d[e];
@@ -340,11 +344,12 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                 for (int e = 0; e < V; ++e) {
                     const T ph = sPh[LG + m0 + e];
                     gc[e] = sG[LG + m0 + e];
-                    t0[e] = (D.E0 + D.B0 * ph) * hh;
-                    t1[e] = (D.E1 + D.B1 * ph) * hh;
+                    t0[e] = rot_factor<T>(D.E0, D.B0, ph, hh);
+                    t1[e] = rot_factor<T>(D.E1, D.B1, ph, hh);
                 }
                 cell_group<T>(sAw + o * arr + c, sAw + (o + 1) * arr + c, da_u, da_d, db_u, db_d,
-                              r0 + il, m0, M, h * sR[il + 1], gc, t0, t1, nu, xi, h, D.cc, true);
+                              r0 + il, m0, M, Rn<T>::mul(h, sR[il + 1]), gc, t0, t1, cn, D.cc,
+                              true);
             }
         };
 

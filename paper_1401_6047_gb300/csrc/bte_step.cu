@@ -42,8 +42,12 @@
  * are bitwise reproducible.  A single instance writes the sample to its
  * trace; a batched instance adds it to its window sums (Eq. absorption_def).
  *
- * Every mbarrier wait is bounded (~2 s of %globaltimer); on expiry the kernel
- * records an error word that the host reports as BTE_ETIMEOUT.
+ * Every mbarrier wait is bounded (~2 s of %globaltimer).  A wait that gives
+ * up on any thread ends the launch at the next row barrier: the producer
+ * issues nothing more, waits (bounded again) for the bulk copies it already
+ * issued, so that no copy is still writing shared memory when the CTA
+ * exits, and the kernel records an error word that the host reports as
+ * BTE_ETIMEOUT.
  */
 #include <cuda_runtime.h>
 
@@ -210,8 +214,10 @@ __device__ __forceinline__ void make_view(View<T>& v, int q, const StepArgs<T>& 
         v.row_a0 = A.row_a0;
         v.col_g = A.col_g;
         v.col_phi = A.col_phi;
-        v.part = A.part;
-        v.ticket = A.ticket;
+        /* a persistent launch may have several steps in flight: slot k % dring */
+        const int slot = A.dring > 1 ? (int)(kbase % A.dring) : 0;
+        v.part = A.part + (size_t)slot * 2 * A.ntx;
+        v.ticket = A.ticket + slot;
         v.N = A.N;
         v.M = A.M;
         v.pitch = A.pitch;
@@ -263,7 +269,45 @@ __device__ __forceinline__ void make_view(View<T>& v, int q, const StepArgs<T>& 
     }
 }
 
-template <typename T, int V, bool BATCH>
+/* Acquire load of a counter at GPU scope. */
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+/* Release store of a counter at GPU scope. */
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+/* Dependencies of item (tx, ty) before its step `target` of a persistent
+ * launch: every item of the 3 x 3 block of tiles and chunks around it must
+ * have completed `target` steps (it reads their rows and halo columns of
+ * the step before, and overwrites the set they read in it).  Called by one
+ * whole warp: lane i < 9 polls neighbour i, so the counters are read in
+ * parallel; the spin is bounded by %globaltimer and stops early when
+ * another CTA has recorded an error.  The result is the same on every
+ * lane: false when the wait gave up. */
+__device__ __forceinline__ bool wait_neighbours(const unsigned* done, int tx, int ty, int ntx,
+                                                int nty, unsigned target, const int* err) {
+    const int lane = threadIdx.x & 31;
+    const int x = tx + lane % 3 - 1, y = ty + lane / 3 - 1;
+    const bool mine = lane < 9 && lane != 4 && x >= 0 && x < ntx && y >= 0 && y < nty;
+    const unsigned* c = done + (size_t)(mine ? y : 0) * ntx + (mine ? x : 0);
+    bool ready = !mine || ld_acquire(c) >= target;
+    if (__all_sync(0xffffffffu, ready)) return true;
+    const uint64_t t0 = global_timer();
+    for (;;) {
+        if (!ready) ready = ld_acquire(c) >= target;
+        if (__all_sync(0xffffffffu, ready)) return true;
+        const bool stop = *reinterpret_cast<const volatile int*>(err) != 0 ||
+                          global_timer() - t0 > kWaitLimitNs;
+        if (__any_sync(0xffffffffu, stop)) return false;
+    }
+}
+
+template <typename T, int V, bool BATCH, bool PERSIST>
 __global__ void __launch_bounds__(MaxBlock<T, V>::value)
     fused_step_kernel(StepArgs<T> A, BatchArgs<T> Bt, int launch_i, int parity) {
     constexpr int H = StepCfg<T>::H;
@@ -291,7 +335,6 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
     const bool is_prod = tid >= NTr;
     const int lane = tid & 31;
     const int items = BATCH ? Bt.items : A.ntx * A.nty;
-    const int cur = (parity + launch_i) & 1;
     const uint32_t rowbytes = (uint32_t)(LW * sizeof(T));
 
     pdl_trigger();
@@ -302,7 +345,8 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
     /* new-row buffers: entries outside the tile's columns +-1 stay zero */
     for (int q = tid; q < 4 * WN; q += blockDim.x) sN[q] = (T)0;
     /* only the counter kernel moves base */
-    const long long kbase = *(BATCH ? Bt.base : A.base) + launch_i;
+    const long long kbase0 = *(BATCH ? Bt.base : A.base) + launch_i;
+    const int cur0 = (parity + launch_i) & 1;
     __syncthreads();
 
     /* everything below reads the previous step's state */
@@ -315,10 +359,10 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
     int p_slot = 0;
     long long p_issued = 0, p_freed = 0;
     /* first item at or after p_item whose instance is still running */
-    auto p_load_item = [&]() {
+    auto p_load_item = [&](long long kb, int cr) {
         while (p_item < items) {
             View<T> v;
-            make_view<T, BATCH>(v, p_item, A, Bt, kbase, cur, false);
+            make_view<T, BATCH>(v, p_item, A, Bt, kb, cr, false);
             if (v.active) {
                 const int ql = p_item - v.q0;
                 const int ty = ql / v.ntx;
@@ -337,7 +381,7 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
             p_item += gridDim.x;
         }
     };
-    auto pump = [&]() {
+    auto pump = [&](long long kb, int cr) {
         while (p_item < items && p_issued < p_freed + RS) {
             const int row = p_n0 - 2 + p_s;
             const uint32_t mb = smem_u32(&bar[p_slot]);
@@ -361,292 +405,362 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
             if (++p_s == p_S) {
                 p_s = 0;
                 p_item += gridDim.x;
-                p_load_item();
+                p_load_item(kb, cr);
             }
         }
     };
-    if (tid == NTr) {
-        p_load_item();
-        pump();
-    }
-
-    bool timed_out = false;
+    bool timed_out = false; /* a bounded wait of this thread gave up        */
+    bool aborted = false;   /* some thread's did: the launch stops          */
     long long cbase = 0; /* global stage index of the current item's stage 0 */
     int c_slot = 0;      /* ring slot of the stage being consumed         */
     uint32_t c_phase = 0;
 
-    for (int q = blockIdx.x; q < items; q += gridDim.x) {
-        View<T> I;
-        make_view<T, BATCH>(I, q, A, Bt, kbase, cur, true);
-        if (!I.active) continue; /* uniform: every thread sees the same instance */
-        const int N = I.N, M = I.M, pitch = I.pitch, ntx = I.ntx;
-        const int ql = q - I.q0;
-        const int ty = ql / ntx;
-        const int tx = ql - ty * ntx;
-        const int n0 = ty * chunk;
-        const int n1 = min(n0 + chunk, N + 1);
-        const int S = n1 - n0 + 4;
-        const int p0 = G + tx * Wt; /* physical column of the tile's first column */
-        const T h = I.h, hh = I.hh, nu = I.nu, xi = I.xi, ccw = I.ccw, ccf = I.ccf;
-
-        __syncthreads(); /* the previous item is done with sR and sN */
-        for (int r = tid; r < n1 - n0 + 2; r += blockDim.x) {
-            const int n = n0 - 1 + r;
-            sR[r] = (n >= 0 && n <= N) ? I.row_a0[n] : (T)0;
+    /* One step: step kbase, reading ping-pong set cur.  A launch runs one
+     * step, or A.nsteps steps of a persistent launch with a grid barrier
+     * between them; the ring's stage counters and barrier phases run on
+     * across steps, and the producer starts a step's copies only after the
+     * barrier, when every CTA's writes of the step before are complete. */
+    auto run_step = [&](const long long kbase, const int cur) {
+        if (tid == NTr) {
+            p_item = blockIdx.x;
+            p_s = 0;
+            p_load_item(kbase, cur);
+            pump(kbase, cur);
         }
 
-        /* per-column constants of the thread's V columns */
-        const int c = p0 + V * tid; /* physical column of the group      */
-        const int lc = H + V * tid; /* its index in a streamed row       */
-        const int ln = V + V * tid; /* its index in a new whole row      */
-        bool ok[V];
-        T g[V], ws[V], we[V], fs[V], fe[V];
-#pragma unroll
-        for (int e = 0; e < V; ++e) {
-            ok[e] = is_comp && (c + e - G) <= M;
-            const T ph = ok[e] ? I.col_phi[c + e] : (T)0;
-            g[e] = ok[e] ? I.col_g[c + e] : (T)0;
-            ws[e] = (I.Ews + I.Bws * ph) * hh;
-            we[e] = (I.Ewe + I.Bwe * ph) * hh;
-            fs[e] = (I.Efs + I.Bfs * ph) * hh;
-            fe[e] = (I.Efe + I.Bfe * ph) * hh;
-        }
-        const bool all_ok = ok[V - 1];
+        for (int q = blockIdx.x; q < items; q += gridDim.x) {
+            View<T> I;
+            make_view<T, BATCH>(I, q, A, Bt, kbase, cur, true);
+            if (!I.active) continue; /* uniform: every thread sees the same instance */
+            const int N = I.N, M = I.M, pitch = I.pitch, ntx = I.ntx;
+            const int ql = q - I.q0;
+            const int ty = ql / ntx;
+            const int tx = ql - ty * ntx;
+            const int n0 = ty * chunk;
+            const int n1 = min(n0 + chunk, N + 1);
+            const int S = n1 - n0 + 4;
+            const int p0 = G + tx * Wt; /* physical column of the tile's first column */
+            using O = Rn<T>;
+            const T h = I.h, hh = I.hh, ccw = I.ccw, ccf = I.ccf;
+            const CnK<T> K = cn_constants<T>(h, I.nu, I.xi);
 
-        /* producer lanes 0/1: the halo columns p0-1 and p0+Wt of new whole rows */
-        const int hcol = (lane == 0) ? p0 - 1 : p0 + Wt;
-        const bool hok = is_prod && lane < 2 && (hcol - G) >= 0 && (hcol - G) <= M;
-        const int hlc = hcol - (p0 - H);
-        const int hidx = (lane == 0) ? V - 1 : V + Wt;
-        T hg = 0, hbs = 0, hbe = 0;
-        if (hok) {
-            hg = I.col_g[hcol];
-            const T ph = I.col_phi[hcol];
-            hbs = (I.Ews + I.Bws * ph) * hh;
-            hbe = (I.Ewe + I.Bwe * ph) * hh;
-        }
-        __syncthreads(); /* sR ready */
-
-        /* rolling windows (registers): old fractional rows j-1, j (own
-         * values and central differences), central differences of new whole
-         * rows j-2, j-1 */
-        T fa_m1[V], fb_m1[V], fa_0[V], fb_0[V];
-        T dfa_m1[V], dfb_m1[V], dfa_0[V], dfb_0[V];
-        T dwa_m2[V], dwb_m2[V], dwa_m1[V], dwb_m1[V];
-#pragma unroll
-        for (int e = 0; e < V; ++e) {
-            fa_m1[e] = fb_m1[e] = fa_0[e] = fb_0[e] = (T)0;
-            dfa_m1[e] = dfb_m1[e] = dfa_0[e] = dfb_0[e] = (T)0;
-            dwa_m2[e] = dwb_m2[e] = dwa_m1[e] = dwb_m1[e] = (T)0;
-        }
-        double part_n = 0.0, part_v = 0.0;
-        int slot_m1 = 0, slot_m2 = 0; /* ring slots of the two previous stages */
-
-        /* stages 0 and 1 (old rows n0-2, n0-1) are consumed as row j+1 of the
-         * load-only iterations j = n0-3, n0-2 */
-        for (int j = n0 - 3; j <= n1; ++j) {
-            if (!mbar_wait(smem_u32(&bar[c_slot]), c_phase)) timed_out = true;
-            const T* ra = sF + (size_t)c_slot * 2 * LW; /* old fractional row j+1 */
-
-            T fa_p1[V], fb_p1[V], dfa_p1[V], dfb_p1[V];
-            if (j + 1 >= 0 && j + 1 <= N && is_comp) {
-                T l, r;
-                ld_own<T, V>(ra + lc, fa_p1);
-                neighbours<T, V>(ra + lc, l, r);
-                diffs<T, V>(fa_p1, l, r, dfa_p1);
-                ld_own<T, V>(ra + LW + lc, fb_p1);
-                neighbours<T, V>(ra + LW + lc, l, r);
-                diffs<T, V>(fb_p1, l, r, dfb_p1);
-            } else {
-#pragma unroll
-                for (int e = 0; e < V; ++e) fa_p1[e] = fb_p1[e] = dfa_p1[e] = dfb_p1[e] = (T)0;
+            __syncthreads(); /* the previous item is done with sR and sN */
+            for (int r = tid; r < n1 - n0 + 2; r += blockDim.x) {
+                const int n = n0 - 1 + r;
+                sR[r] = (n >= 0 && n <= N) ? I.row_a0[n] : (T)0;
             }
 
-            if (j >= n0 - 1) {
-                /* ---- new whole-grid row j ---- */
-                const bool wrow_ok = j >= 0 && j <= N;
-                T wa_n[V], wb_n[V];
-                T* na = sN + (size_t)(j & 1) * 2 * WN;
-                if (wrow_ok) {
-                    const T nf = (T)j;
-                    const T chi = (j == 1) ? (T)2 : (T)1;
-                    const T ha0 = h * sR[j - n0 + 1];
-                    const T* wa = sW + (size_t)slot_m1 * 2 * LW; /* old whole row j */
-                    if (is_comp) {
-                        T oa[V], ob[V];
-                        ld_own<T, V>(wa + lc, oa);
-                        ld_own<T, V>(wa + LW + lc, ob);
+            /* per-column constants of the thread's V columns */
+            const int c = p0 + V * tid; /* physical column of the group      */
+            const int lc = H + V * tid; /* its index in a streamed row       */
+            const int ln = V + V * tid; /* its index in a new whole row      */
+            bool ok[V];
+            T g[V], ws[V], we[V], fs[V], fe[V];
+    #pragma unroll
+            for (int e = 0; e < V; ++e) {
+                ok[e] = is_comp && (c + e - G) <= M;
+                const T ph = ok[e] ? I.col_phi[c + e] : (T)0;
+                g[e] = ok[e] ? I.col_g[c + e] : (T)0;
+                ws[e] = rot_factor<T>(I.Ews, I.Bws, ph, hh);
+                we[e] = rot_factor<T>(I.Ewe, I.Bwe, ph, hh);
+                fs[e] = rot_factor<T>(I.Efs, I.Bfs, ph, hh);
+                fe[e] = rot_factor<T>(I.Efe, I.Bfe, ph, hh);
+            }
+            const bool all_ok = ok[V - 1];
+
+            /* producer lane 0: the halo columns p0-1 and p0+Wt of new whole
+             * rows, as one pair of cells (the same paired arithmetic as the
+             * compute threads' cells) */
+            const bool hlane = is_prod && lane == 0;
+            bool hok[2];
+            int hlc[2], hidx[2];
+            T hg[2], hbs[2], hbe[2];
 #pragma unroll
-                        for (int e = 0; e < V; ++e) {
-                            T an, bn;
-                            cn_cell<T>(oa[e], ob[e], ccw * (dfb_p1[e] - dfb_m1[e]),
-                                       ccw * (chi * dfa_m1[e] - dfa_p1[e]), ha0 * g[e], nf * ws[e],
-                                       nf * we[e], nu, xi, h, an, bn);
-                            wa_n[e] = ok[e] ? an : (T)0;
-                            wb_n[e] = (ok[e] && j > 0) ? bn : (T)0;
-                        }
-                        st_own<T, V>(na + ln, wa_n);
-                        st_own<T, V>(na + WN + ln, wb_n);
-                        if (j >= n0 && j < n1) {
-                            T* wrow = I.oWa + (size_t)j * pitch + c;
-                            if (all_ok) {
-                                st_own<T, V>(wrow, wa_n);
-                                st_own<T, V>(wrow + I.dWb, wb_n);
-                            } else {
-#pragma unroll
-                                for (int e = 0; e < V; ++e)
-                                    if (ok[e]) {
-                                        wrow[e] = wa_n[e];
-                                        wrow[I.dWb + e] = wb_n[e];
-                                    }
-                            }
-                        }
-                        if (n0 == 0 && j <= 1) {
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const int hcol = s2 == 0 ? p0 - 1 : p0 + Wt;
+                hok[s2] = hlane && (hcol - G) >= 0 && (hcol - G) <= M;
+                hlc[s2] = hcol - (p0 - H);
+                hidx[s2] = s2 == 0 ? V - 1 : V + Wt;
+                hg[s2] = hbs[s2] = hbe[s2] = (T)0;
+                if (hok[s2]) {
+                    hg[s2] = I.col_g[hcol];
+                    const T ph = I.col_phi[hcol];
+                    hbs[s2] = rot_factor<T>(I.Ews, I.Bws, ph, hh);
+                    hbe[s2] = rot_factor<T>(I.Ewe, I.Bwe, ph, hh);
+                }
+            }
+            __syncthreads(); /* sR ready */
+
+            /* rolling windows (registers): old fractional rows j-1, j (own
+             * values and central differences), central differences of new whole
+             * rows j-2, j-1 */
+            T fa_m1[V], fb_m1[V], fa_0[V], fb_0[V];
+            T dfa_m1[V], dfb_m1[V], dfa_0[V], dfb_0[V];
+            T dwa_m2[V], dwb_m2[V], dwa_m1[V], dwb_m1[V];
+    #pragma unroll
+            for (int e = 0; e < V; ++e) {
+                fa_m1[e] = fb_m1[e] = fa_0[e] = fb_0[e] = (T)0;
+                dfa_m1[e] = dfb_m1[e] = dfa_0[e] = dfb_0[e] = (T)0;
+                dwa_m2[e] = dwb_m2[e] = dwa_m1[e] = dwb_m1[e] = (T)0;
+            }
+            double part_n = 0.0, part_v = 0.0;
+            int slot_m1 = 0, slot_m2 = 0; /* ring slots of the two previous stages */
+
+            /* stages 0 and 1 (old rows n0-2, n0-1) are consumed as row j+1 of the
+             * load-only iterations j = n0-3, n0-2 */
+            for (int j = n0 - 3; j <= n1; ++j) {
+                if (!mbar_wait(smem_u32(&bar[c_slot]), c_phase)) timed_out = true;
+                const T* ra = sF + (size_t)c_slot * 2 * LW; /* old fractional row j+1 */
+
+                T fa_p1[V], fb_p1[V], dfa_p1[V], dfb_p1[V];
+                if (j + 1 >= 0 && j + 1 <= N && is_comp) {
+                    T l, r;
+                    ld_own<T, V>(ra + lc, fa_p1);
+                    neighbours<T, V>(ra + lc, l, r);
+                    diffs<T, V>(fa_p1, l, r, dfa_p1);
+                    ld_own<T, V>(ra + LW + lc, fb_p1);
+                    neighbours<T, V>(ra + LW + lc, l, r);
+                    diffs<T, V>(fb_p1, l, r, dfb_p1);
+                } else {
+    #pragma unroll
+                    for (int e = 0; e < V; ++e) fa_p1[e] = fb_p1[e] = dfa_p1[e] = dfb_p1[e] = (T)0;
+                }
+
+                if (j >= n0 - 1) {
+                    /* ---- new whole-grid row j ---- */
+                    const bool wrow_ok = j >= 0 && j <= N;
+                    T wa_n[V], wb_n[V];
+                    T* na = sN + (size_t)(j & 1) * 2 * WN;
+                    if (wrow_ok) {
+                        const T nf = (T)j;
+                        const T chi = (j == 1) ? (T)2 : (T)1;
+                        const T hr = O::mul(h, sR[j - n0 + 1]);
+                        const T* wa = sW + (size_t)slot_m1 * 2 * LW; /* old whole row j */
+                        if (is_comp) {
+                            T oa[V], ob[V];
+                            ld_own<T, V>(wa + lc, oa);
+                            ld_own<T, V>(wa + LW + lc, ob);
+                                T an[V], bn[V];
+                            cn_row<T, V>(oa, ob, dfb_p1, dfb_m1, dfa_m1, dfa_p1, ccw, chi, hr, g,
+                                         nf, ws, we, K, an, bn);
 #pragma unroll
                             for (int e = 0; e < V; ++e) {
-                                if (j == 0) part_n += (double)wa_n[e];
-                                if (j == 1) part_v += (double)wb_n[e];
+                                wa_n[e] = ok[e] ? an[e] : (T)0;
+                                wb_n[e] = (ok[e] && j > 0) ? bn[e] : (T)0;
                             }
-                        }
-                    } else if (is_prod && lane < 2) {
-                        T an = 0, bn = 0;
-                        if (hok) {
+                            st_own<T, V>(na + ln, wa_n);
+                            st_own<T, V>(na + WN + ln, wb_n);
+                            if (j >= n0 && j < n1) {
+                                T* wrow = I.oWa + (size_t)j * pitch + c;
+                                if (all_ok) {
+                                    st_own<T, V>(wrow, wa_n);
+                                    st_own<T, V>(wrow + I.dWb, wb_n);
+                                } else {
+    #pragma unroll
+                                    for (int e = 0; e < V; ++e)
+                                        if (ok[e]) {
+                                            wrow[e] = wa_n[e];
+                                            wrow[I.dWb + e] = wb_n[e];
+                                        }
+                                }
+                            }
+                            if (n0 == 0 && j <= 1) {
+    #pragma unroll
+                                for (int e = 0; e < V; ++e) {
+                                    if (j == 0) part_n += (double)wa_n[e];
+                                    if (j == 1) part_v += (double)wb_n[e];
+                                }
+                            }
+                        } else if (hlane) {
                             const T* fd = sF + (size_t)slot_m2 * 2 * LW; /* old frac row j-1 */
                             const bool dn = j - 1 >= 0, up = j + 1 <= N;
-                            const T Dad = dn ? fd[hlc + 1] - fd[hlc - 1] : (T)0;
-                            const T Dbd = dn ? fd[LW + hlc + 1] - fd[LW + hlc - 1] : (T)0;
-                            const T Dau = up ? ra[hlc + 1] - ra[hlc - 1] : (T)0;
-                            const T Dbu = up ? ra[LW + hlc + 1] - ra[LW + hlc - 1] : (T)0;
-                            cn_cell<T>(wa[hlc], wa[LW + hlc], ccw * (Dbu - Dbd), ccw * (chi * Dad - Dau),
-                                       ha0 * hg, nf * hbs, nf * hbe, nu, xi, h, an, bn);
-                            if (j == 0) bn = (T)0;
+                            T oa2[2], ob2[2], dad[2], dbd[2], dau[2], dbu[2], an2[2], bn2[2];
+#pragma unroll
+                            for (int s2 = 0; s2 < 2; ++s2) {
+                                const int c2 = hlc[s2];
+                                oa2[s2] = wa[c2];
+                                ob2[s2] = wa[LW + c2];
+                                dad[s2] = dn ? fd[c2 + 1] - fd[c2 - 1] : (T)0;
+                                dbd[s2] = dn ? fd[LW + c2 + 1] - fd[LW + c2 - 1] : (T)0;
+                                dau[s2] = up ? ra[c2 + 1] - ra[c2 - 1] : (T)0;
+                                dbu[s2] = up ? ra[LW + c2 + 1] - ra[LW + c2 - 1] : (T)0;
+                            }
+                            cn_row<T, 2>(oa2, ob2, dbu, dbd, dad, dau, ccw, chi, hr, hg, nf, hbs,
+                                         hbe, K, an2, bn2);
+#pragma unroll
+                            for (int s2 = 0; s2 < 2; ++s2) {
+                                na[hidx[s2]] = hok[s2] ? an2[s2] : (T)0;
+                                na[WN + hidx[s2]] = (hok[s2] && j > 0) ? bn2[s2] : (T)0;
+                            }
                         }
-                        na[hidx] = an;
-                        na[WN + hidx] = bn;
                     }
-                }
-                __syncthreads();
-                if (tid == NTr) {
-                    /* every stage up to old row j-1 has been read for the last time */
-                    const long long si = j - n0 + 3;
-                    const long long f = (j == n1) ? cbase + S : cbase + si - 1;
-                    if (f > p_freed) p_freed = f;
-                    fence_proxy_async_smem();
-                    pump();
-                }
+                    /* the row barrier; it also ends the launch when a wait gave up */
+                    if (__syncthreads_or(timed_out)) {
+                        aborted = true;
+                        if (tid == 0) atomicExch(BATCH ? Bt.err : A.err, kErrTimeout);
+                        break;
+                    }
+                    if (tid == NTr) {
+                        /* every stage up to old row j-1 has been read for the last time */
+                        const long long si = j - n0 + 3;
+                        const long long f = (j == n1) ? cbase + S : cbase + si - 1;
+                        if (f > p_freed) p_freed = f;
+                        fence_proxy_async_smem();
+                        pump(kbase, cur);
+                    }
 
-                /* ---- new fractional row j-1 ---- */
-                T dwa_0[V], dwb_0[V];
-                if (wrow_ok && is_comp) {
-                    T l, r;
-                    neighbours<T, V>(na + ln, l, r);
-                    diffs<T, V>(wa_n, l, r, dwa_0);
-                    neighbours<T, V>(na + WN + ln, l, r);
-                    diffs<T, V>(wb_n, l, r, dwb_0);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < V; ++e) dwa_0[e] = dwb_0[e] = (T)0;
-                }
-                const int r = j - 1;
-                if (r >= n0 && r < n1 && is_comp && ok[0]) {
-                    const T nf = (T)r;
-                    const T chi = (r == 1) ? (T)2 : (T)1;
-                    const T ha0 = h * sR[r - n0 + 1];
-                    T fa_n[V], fb_n[V];
-#pragma unroll
-                    for (int e = 0; e < V; ++e) {
-                        cn_cell<T>(fa_m1[e], fb_m1[e], ccf * (dwb_0[e] - dwb_m2[e]),
-                                   ccf * (chi * dwa_m2[e] - dwa_0[e]), ha0 * g[e], nf * fs[e],
-                                   nf * fe[e], nu, xi, h, fa_n[e], fb_n[e]);
-                        if (r == 0) fb_n[e] = (T)0;
-                    }
-                    T* frow = I.oFa + (size_t)r * pitch + c;
-                    if (all_ok) {
-                        st_own<T, V>(frow, fa_n);
-                        st_own<T, V>(frow + I.dFb, fb_n);
+                    /* ---- new fractional row j-1 ---- */
+                    T dwa_0[V], dwb_0[V];
+                    if (wrow_ok && is_comp) {
+                        T l, r;
+                        neighbours<T, V>(na + ln, l, r);
+                        diffs<T, V>(wa_n, l, r, dwa_0);
+                        neighbours<T, V>(na + WN + ln, l, r);
+                        diffs<T, V>(wb_n, l, r, dwb_0);
                     } else {
-#pragma unroll
-                        for (int e = 0; e < V; ++e)
-                            if (ok[e]) {
-                                frow[e] = fa_n[e];
-                                frow[I.dFb + e] = fb_n[e];
-                            }
+    #pragma unroll
+                        for (int e = 0; e < V; ++e) dwa_0[e] = dwb_0[e] = (T)0;
                     }
-                }
-
-                /* ---- observables of rows 0 and 1 ---- */
-                if (n0 == 0 && j == 1) {
-                    const double sn = block_sum(part_n, red);
-                    const double sv = block_sum(part_v, red);
-                    if (tid == 0) {
-                        I.part[tx] = sn;
-                        I.part[ntx + tx] = sv;
-                        __threadfence();
-                        const unsigned t = atomicAdd(I.ticket, 1u);
-                        if (t == (unsigned)(ntx - 1)) {
-                            __threadfence();
-                            double s_n = 0, s_v = 0;
-                            const volatile double* pv = I.part;
-                            for (int u = 0; u < ntx; ++u) {
-                                s_n += pv[u];
-                                s_v += pv[ntx + u];
-                            }
-                            if constexpr (!BATCH) {
-                                A.trace_n[kbase + 1] = A.nscale * s_n;
-                                A.trace_v[kbase + 1] = A.vscale * s_v;
-                            } else {
-                                /* window sums of Eq. absorption_def, FP64, one writer
-                                 * per instance and step */
-                                const BatchInst<T>& B = Bt.inst[I.inst];
-                                const double vv = B.vscale * s_v, nn = B.nscale * s_n;
-                                const long long k1 = kbase + 1;
-                                double* acc = B.acc;
-                                if (k1 > B.K - B.Kw) {
-                                    const double ang =
-                                        B.P > 0 ? 6.283185307179586476925286766559 *
-                                                      (double)(k1 % B.P) / (double)B.P
-                                                : B.omega * (double)k1 * B.dt_eff;
-                                    acc[0] += vv * cos(ang);
-                                    acc[1] += vv;
+                    const int r = j - 1;
+                    if (r >= n0 && r < n1 && is_comp && ok[0]) {
+                        const T nf = (T)r;
+                        const T chi = (r == 1) ? (T)2 : (T)1;
+                        const T hr = O::mul(h, sR[r - n0 + 1]);
+                        T fa_n[V], fb_n[V];
+                            cn_row<T, V>(fa_m1, fb_m1, dwb_0, dwb_m2, dwa_m2, dwa_0, ccf, chi, hr, g,
+                                     nf, fs, fe, K, fa_n, fb_n);
+                        if (r == 0) {
+#pragma unroll
+                            for (int e = 0; e < V; ++e) fb_n[e] = (T)0;
+                        }
+                        T* frow = I.oFa + (size_t)r * pitch + c;
+                        if (all_ok) {
+                            st_own<T, V>(frow, fa_n);
+                            st_own<T, V>(frow + I.dFb, fb_n);
+                        } else {
+    #pragma unroll
+                            for (int e = 0; e < V; ++e)
+                                if (ok[e]) {
+                                    frow[e] = fa_n[e];
+                                    frow[I.dFb + e] = fb_n[e];
                                 }
-                                acc[2] = fmax(acc[2], fabs(nn - 1.0));
-                                if (!isfinite(vv) || !isfinite(nn)) acc[3] = 1.0;
-                                acc[4] = vv;
-                                acc[5] = nn;
-                            }
-                            *I.ticket = 0u;
                         }
                     }
+
+                    /* ---- observables of rows 0 and 1 ---- */
+                    if (n0 == 0 && j == 1) {
+                        const double sn = block_sum(part_n, red);
+                        const double sv = block_sum(part_v, red);
+                        if (tid == 0) {
+                            I.part[tx] = sn;
+                            I.part[ntx + tx] = sv;
+                            __threadfence();
+                            const unsigned t = atomicAdd(I.ticket, 1u);
+                            if (t == (unsigned)(ntx - 1)) {
+                                __threadfence();
+                                double s_n = 0, s_v = 0;
+                                const volatile double* pv = I.part;
+                                for (int u = 0; u < ntx; ++u) {
+                                    s_n += pv[u];
+                                    s_v += pv[ntx + u];
+                                }
+                                if constexpr (!BATCH) {
+                                    A.trace_n[kbase + 1] = A.nscale * s_n;
+                                    A.trace_v[kbase + 1] = A.vscale * s_v;
+                                } else {
+                                    /* window sums of Eq. absorption_def, FP64, one writer
+                                     * per instance and step */
+                                    const BatchInst<T>& B = Bt.inst[I.inst];
+                                    const double vv = B.vscale * s_v, nn = B.nscale * s_n;
+                                    const long long k1 = kbase + 1;
+                                    double* acc = B.acc;
+                                    if (k1 > B.K - B.Kw) {
+                                        const double ang =
+                                            B.P > 0 ? 6.283185307179586476925286766559 *
+                                                          (double)(k1 % B.P) / (double)B.P
+                                                    : B.omega * (double)k1 * B.dt_eff;
+                                        acc[0] += vv * cos(ang);
+                                        acc[1] += vv;
+                                    }
+                                    acc[2] = fmax(acc[2], fabs(nn - 1.0));
+                                    if (!isfinite(vv) || !isfinite(nn)) acc[3] = 1.0;
+                                    acc[4] = vv;
+                                    acc[5] = nn;
+                                }
+                                *I.ticket = 0u;
+                            }
+                        }
+                    }
+    #pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        dwa_m2[e] = dwa_m1[e];
+                        dwb_m2[e] = dwb_m1[e];
+                        dwa_m1[e] = dwa_0[e];
+                        dwb_m1[e] = dwb_0[e];
+                    }
                 }
-#pragma unroll
+    #pragma unroll
                 for (int e = 0; e < V; ++e) {
-                    dwa_m2[e] = dwa_m1[e];
-                    dwb_m2[e] = dwb_m1[e];
-                    dwa_m1[e] = dwa_0[e];
-                    dwb_m1[e] = dwb_0[e];
+                    fa_m1[e] = fa_0[e];
+                    fb_m1[e] = fb_0[e];
+                    fa_0[e] = fa_p1[e];
+                    fb_0[e] = fb_p1[e];
+                    dfa_m1[e] = dfa_0[e];
+                    dfb_m1[e] = dfb_0[e];
+                    dfa_0[e] = dfa_p1[e];
+                    dfb_0[e] = dfb_p1[e];
+                }
+                slot_m2 = slot_m1;
+                slot_m1 = c_slot;
+                if (++c_slot == RS) {
+                    c_slot = 0;
+                    c_phase ^= 1u;
                 }
             }
-#pragma unroll
-            for (int e = 0; e < V; ++e) {
-                fa_m1[e] = fa_0[e];
-                fb_m1[e] = fb_0[e];
-                fa_0[e] = fa_p1[e];
-                fb_0[e] = fb_p1[e];
-                dfa_m1[e] = dfa_0[e];
-                dfb_m1[e] = dfb_0[e];
-                dfa_0[e] = dfa_p1[e];
-                dfb_0[e] = dfb_p1[e];
+            if (aborted) break;
+            cbase += S;
+        }
+    };
+    if constexpr (!PERSIST) {
+        run_step(kbase0, cur0);
+    } else {
+        /* one item per CTA (gridDim.x == ntx * nty), every step */
+        const int tx = (int)blockIdx.x % A.ntx, ty = (int)blockIdx.x / A.ntx;
+        for (int st = 0; st < A.nsteps; ++st) {
+            if (st > 0) {
+                bool gave_up = false;
+                if (tid < 32)
+                    gave_up = !wait_neighbours(A.done, tx, ty, A.ntx, A.nty, (unsigned)st, A.err);
+                if (__syncthreads_or(gave_up)) {
+                    aborted = true;
+                    if (tid == 0) atomicExch(A.err, kErrTimeout);
+                    break;
+                }
+                /* the neighbours' stores, seen by this CTA's bulk copies (async proxy) */
+                if (tid == NTr) asm volatile("fence.proxy.async.global;" ::: "memory");
             }
-            slot_m2 = slot_m1;
-            slot_m1 = c_slot;
-            if (++c_slot == RS) {
-                c_slot = 0;
-                c_phase ^= 1u;
+            run_step(kbase0 + st, (cur0 + st) & 1);
+            if (aborted) break;
+            /* this thread's stores of the step, before another CTA's bulk
+             * copies read them; then the item's completion count */
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                st_release(A.done + blockIdx.x, (unsigned)(st + 1));
             }
         }
-        cbase += S;
     }
-    if (timed_out) atomicExch(BATCH ? Bt.err : A.err, kErrTimeout);
+    if (aborted && tid == NTr) {
+        /* Drain: every stage issued and not yet seen complete lies among the
+         * last RS issued (a slot is re-armed only after a row barrier that no
+         * timeout preceded), and no slot holds two of them, so stage s
+         * completes phase (s / RS) & 1 of slot s % RS. */
+        const long long first = p_issued > RS ? p_issued - RS : 0;
+        for (long long s = first; s < p_issued; ++s)
+            if (!mbar_wait(smem_u32(&bar[(int)(s % RS)]), (uint32_t)((s / RS) & 1))) break;
+    }
+    if ((timed_out || aborted) && tid == 0) atomicExch(BATCH ? Bt.err : A.err, kErrTimeout);
 }
 
 }  // namespace
@@ -671,19 +785,20 @@ int step_max_tile(int vec) {
     return 2 * (MaxBlock<double, 2>::value - 32);
 }
 
-template <typename T, bool BATCH>
+template <typename T, bool BATCH, bool PERSIST>
 static const void* step_fn(int vec) {
     if constexpr (sizeof(T) == 4)
-        return vec == 4 ? reinterpret_cast<const void*>(&fused_step_kernel<float, 4, BATCH>)
-                        : reinterpret_cast<const void*>(&fused_step_kernel<float, 2, BATCH>);
+        return vec == 4
+                   ? reinterpret_cast<const void*>(&fused_step_kernel<float, 4, BATCH, PERSIST>)
+                   : reinterpret_cast<const void*>(&fused_step_kernel<float, 2, BATCH, PERSIST>);
     else
-        return reinterpret_cast<const void*>(&fused_step_kernel<double, 2, BATCH>);
+        return reinterpret_cast<const void*>(&fused_step_kernel<double, 2, BATCH, PERSIST>);
 }
 
-template <typename T, bool BATCH>
+template <typename T, bool BATCH, bool PERSIST>
 static int configure(int tile_m, int chunk_n, int vec, int* blocks_per_sm) {
     const size_t bytes = step_smem_bytes<T>(tile_m, chunk_n, vec);
-    const void* fn = step_fn<T, BATCH>(vec);
+    const void* fn = step_fn<T, BATCH, PERSIST>(vec);
     cudaError_t e =
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;
@@ -697,15 +812,20 @@ static int configure(int tile_m, int chunk_n, int vec, int* blocks_per_sm) {
 
 template <typename T>
 int step_kernel_configure(int tile_m, int chunk_n, int vec, int* blocks_per_sm) {
-    return configure<T, false>(tile_m, chunk_n, vec, blocks_per_sm);
+    return configure<T, false, false>(tile_m, chunk_n, vec, blocks_per_sm);
+}
+
+template <typename T>
+int step_kernel_configure_persist(int tile_m, int chunk_n, int vec, int* blocks_per_sm) {
+    return configure<T, false, true>(tile_m, chunk_n, vec, blocks_per_sm);
 }
 
 template <typename T>
 int step_kernel_configure_batch(int tile_m, int chunk_n, int vec, int* blocks_per_sm) {
-    return configure<T, true>(tile_m, chunk_n, vec, blocks_per_sm);
+    return configure<T, true, false>(tile_m, chunk_n, vec, blocks_per_sm);
 }
 
-template <typename T, bool BATCH>
+template <typename T, bool BATCH, bool PERSIST>
 static int launch(const StepArgs<T>& a, const BatchArgs<T>& b, int grid, int tile_m, int chunk_n,
                   int vec, int i, int parity, bool pdl, void* stream) {
     cudaLaunchConfig_t cfg = {};
@@ -714,18 +834,24 @@ static int launch(const StepArgs<T>& a, const BatchArgs<T>& b, int grid, int til
     cfg.dynamicSmemBytes = step_smem_bytes<T>(tile_m, chunk_n, vec);
     cfg.stream = (cudaStream_t)stream;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+    if (PERSIST) {
+        /* every CTA must be resident at once (the grid barrier waits for all) */
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+    } else {
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+    }
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaError_t e;
     if constexpr (sizeof(T) == 4) {
         if (vec == 4)
-            e = cudaLaunchKernelEx(&cfg, fused_step_kernel<float, 4, BATCH>, a, b, i, parity);
+            e = cudaLaunchKernelEx(&cfg, fused_step_kernel<float, 4, BATCH, PERSIST>, a, b, i, parity);
         else
-            e = cudaLaunchKernelEx(&cfg, fused_step_kernel<float, 2, BATCH>, a, b, i, parity);
+            e = cudaLaunchKernelEx(&cfg, fused_step_kernel<float, 2, BATCH, PERSIST>, a, b, i, parity);
     } else {
-        e = cudaLaunchKernelEx(&cfg, fused_step_kernel<double, 2, BATCH>, a, b, i, parity);
+        e = cudaLaunchKernelEx(&cfg, fused_step_kernel<double, 2, BATCH, PERSIST>, a, b, i, parity);
     }
     if (e != cudaSuccess) return (int)e;
     return ok_or(cudaGetLastError());
@@ -734,13 +860,22 @@ static int launch(const StepArgs<T>& a, const BatchArgs<T>& b, int grid, int til
 template <typename T>
 int launch_step(const StepArgs<T>& a, int i, int parity, bool pdl, void* stream) {
     BatchArgs<T> none = {};
-    return launch<T, false>(a, none, a.grid, a.tile_m, a.chunk_n, a.vec, i, parity, pdl, stream);
+    return launch<T, false, false>(a, none, a.grid, a.tile_m, a.chunk_n, a.vec, i, parity, pdl,
+                                   stream);
+}
+
+template <typename T>
+int launch_step_persist(const StepArgs<T>& a, int parity, void* stream) {
+    BatchArgs<T> none = {};
+    return launch<T, false, true>(a, none, a.grid, a.tile_m, a.chunk_n, a.vec, 0, parity, false,
+                                  stream);
 }
 
 template <typename T>
 int launch_step_batch(const BatchArgs<T>& b, int i, int parity, bool pdl, void* stream) {
     StepArgs<T> none = {};
-    return launch<T, true>(none, b, b.grid, b.tile_m, b.chunk_n, b.vec, i, parity, pdl, stream);
+    return launch<T, true, false>(none, b, b.grid, b.tile_m, b.chunk_n, b.vec, i, parity, pdl,
+                                  stream);
 }
 
 #define BTE_STEP_INSTANTIATE(T)                                                    \
@@ -749,7 +884,9 @@ int launch_step_batch(const BatchArgs<T>& b, int i, int parity, bool pdl, void* 
     template int step_max_tile<T>(int);                                            \
     template int step_kernel_configure<T>(int, int, int, int*);                    \
     template int step_kernel_configure_batch<T>(int, int, int, int*);              \
+    template int step_kernel_configure_persist<T>(int, int, int, int*);            \
     template int launch_step<T>(const StepArgs<T>&, int, int, bool, void*);        \
+    template int launch_step_persist<T>(const StepArgs<T>&, int, void*);           \
     template int launch_step_batch<T>(const BatchArgs<T>&, int, int, bool, void*);
 BTE_STEP_INSTANTIATE(float)
 BTE_STEP_INSTANTIATE(double)

@@ -75,13 +75,20 @@ def test_invalid_parameters_rejected_on_host(bad):
 def test_on_chip_single_instance_mode_is_planned_on_host():
     """resident=1 (one cluster holds the grid): a grid that fits plans with
     the same device layout as the streamed mode; one that does not fit any
-    16-CTA cluster, or a bad flag, is rejected before any CUDA call."""
+    16-CTA cluster, or a bad flag, is rejected before any CUDA call.
+    resident=2 (persistent launches) plans the streamed layout, plus its
+    dependency counters, for any grid."""
     p = W.c1_fp64()
     assert bte.workspace_size(p, resident=1) == bte.workspace_size(p)
     with pytest.raises(bte.BteError) as e:
         bte.workspace_size(W.c2(), resident=1)  # 401 x 4001: about 26 MB of state
     assert e.value.code == bte.EINVAL
-    for bad in (dict(resident=2), dict(reserved=1)):
+    # resident=2 (persistent launches): the streamed layout plus the per-item
+    # completion counters and ntx + 1 slots of row-0 partial sums, any grid
+    ws0, ws2 = bte.workspace_size(W.c2()), bte.workspace_size(W.c2(), resident=2)
+    shape = bte.launch_shape(W.c2())
+    assert ws0 < ws2 <= ws0 + 4096 * (shape["grid_x"] + 1) + 4 * shape["grid_x"] * shape["grid_y"] + 1024
+    for bad in (dict(resident=3), dict(resident=-1), dict(reserved=1)):
         t = bte._tuning()
         for k, v in bad.items():
             setattr(t, k, v)

@@ -86,12 +86,18 @@ def test_low_temperature_fp64_matches_oracle():
     p = W.Params(E_dc=6.0, E_omega=0.1, omega=3.0, B=4.0, mu=116.0, alpha=0.9496, n_max=60,
                  m_points=1201, phiy_min=-6.0, phiy_max=6.0, dt=2e-3, periods=12.0,
                  avg_window=1.0)
-    ref = oracle.solve(p)
-    o = bte.solve(p)
-    assert o.status == bte.OK
-    assert abs(o.absorption - ref.A) <= RTOL64 * abs(ref.A)
-    assert abs(o.v_dc_avg - ref.v_dc) <= RTOL64 * abs(ref.v_dc)
-    assert abs(o.norm_max_abs_err - ref.norm_err) <= 1e-13
+    ref = oracle.solve(p, want_state=True)
+    with bte.Solver(p) as s:
+        s.run()
+        o = s.observables()
+        assert o.status == bte.OK
+        assert abs(o.absorption - ref.A) <= RTOL64 * abs(ref.A)
+        assert abs(o.v_dc_avg - ref.v_dc) <= RTOL64 * abs(ref.v_dc)
+        assert abs(o.norm_max_abs_err - ref.norm_err) <= 1e-13
+        # every harmonic of both grids, not only the rows the observables read
+        _cmp_state(s, ref.state, RTOL64, "low temperature final state")
+        v, _ = s.trace()
+        assert _rel_arr(v, ref.v) <= RTOL64
 
 
 @pytest.mark.parametrize("shape", SHAPES)

@@ -4,10 +4,14 @@ Tolerances.  The tensor-core layers read bfloat16 activations and weights
 (unit roundoff 2^-9).  Against the reference evaluated with the same
 bfloat16 roundings (``mixed=True``) the GPU differs only by FP32
 accumulation order, __expf in the activation, and the rare bfloat16
-rounding those flip: outputs within 2e-3 of their RMS, gradients within
-1e-2 per tensor (norm-wise).  Against the plain FP64 network the bfloat16
-roundings themselves count: outputs within 3e-2 of their RMS, gradients
-within 5e-2 per tensor.
+rounding those flip: outputs within 2e-3 of their RMS.  Gradients are
+compared element by element: for every parameter tensor,
+max |g_gpu - g_ref| <= 1e-2 max |g_ref|.  A flipped bfloat16 rounding moves
+one back-propagated entry by one bfloat16 ulp (2^-8 of it), and a weight
+gradient entry sums 200 such products, so one flip shifts it by well under
+1e-3 of the tensor's largest entry.  Against the plain FP64 network the
+bfloat16 roundings themselves count: outputs within 3e-2 of their RMS,
+gradients element-wise within 5e-2 of the tensor's largest entry.
 """
 import numpy as np
 import pytest
@@ -46,28 +50,83 @@ def test_forward_ensemble_matches_reference():
     assert np.array_equal(mask, np.max(std, axis=1) > 1e-3)
 
 
-def test_gradients_match_reference():
-    """bte_sur_grad against the reference backward pass (p11)."""
-    M = 3
+def _elementwise(g, ref):
+    """Largest entry-wise error of a tensor relative to its largest entry."""
+    return float(np.max(np.abs(g - ref)) / np.max(np.abs(ref)))
+
+
+GRAD_TOL = {True: 1e-2, False: 5e-2}  # mixed (bfloat16-emulating) / plain FP64 reference
+
+
+def _grad_case(M=3, B=200):
     p = S.init_params(M, seed=2)
     rng = np.random.default_rng(5)
-    x = W.sweep_matrix(200, 6)
-    t = np.stack([rng.normal(Y_MEAN[0], Y_STD[0], 200), rng.normal(Y_MEAN[1], Y_STD[1], 200)], axis=1)
-    with S.Surrogate(Y_MEAN, Y_STD, members=M, batch_capacity=256) as sur:
-        sur.set_params(p)
-        loss, g = sur.grad(x, t)
+    x = W.sweep_matrix(B, 6)
+    t = np.stack([rng.normal(Y_MEAN[0], Y_STD[0], B), rng.normal(Y_MEAN[1], Y_STD[1], B)], axis=1)
     lo, hi = S.box_bounds()
     xh = mlp.normalise_x(x, lo, hi)
     th = (t - np.array(Y_MEAN)) / np.array(Y_STD)
+    return p, x, t, xh, th
+
+
+def test_gradients_match_reference():
+    """bte_sur_grad against the reference backward pass, element by element
+    for every parameter tensor of every member (p11)."""
+    M = 3
+    p, x, t, xh, th = _grad_case(M)
+    with S.Surrogate(Y_MEAN, Y_STD, members=M, batch_capacity=256) as sur:
+        sur.set_params(p)
+        loss, g = sur.grad(x, t)
+    worst = {}
     for m in range(M):
         pm = mlp.unpack(p[m].astype(np.float64))
         gm = mlp.unpack(g[m].astype(np.float64))
-        for mixed, tol in ((True, 1e-2), (False, 5e-2)):
+        for mixed in (True, False):
             L, gr = mlp.loss_and_grad(pm, xh, th, mixed)
             assert abs(loss[m] - L) <= 1e-2 * L
             for k in gr:
-                err = np.linalg.norm(gm[k] - gr[k]) / np.linalg.norm(gr[k])
-                assert err <= tol, (m, k, mixed, err)
+                err = _elementwise(gm[k], gr[k])
+                worst[(mixed, k)] = max(worst.get((mixed, k), 0.0), err)
+                assert err <= GRAD_TOL[mixed], (m, k, mixed, err)
+    print("element-wise gradient error / max|g_ref|:",
+          {f"{'mixed' if a else 'fp64'}:{k}": f"{v:.2e}" for (a, k), v in sorted(worst.items())})
+
+
+def test_gradient_check_catches_planted_mistakes(monkeypatch):
+    """Mistakes planted in the reference (on the CPU) that an element-wise
+    comparison with the GPU gradient must reject: two entries of dW2
+    exchanged across the diagonal (a transposed index confined to one
+    pair), the b3 gradient read one unit off, and the SiLU' factor dropped
+    from the first layer's back-propagation."""
+    p, x, t, xh, th = _grad_case(1)
+    with S.Surrogate(Y_MEAN, Y_STD, members=1, batch_capacity=256) as sur:
+        sur.set_params(p)
+        _, g = sur.grad(x, t)
+    pm = mlp.unpack(p[0].astype(np.float64))
+    gm = mlp.unpack(g[0].astype(np.float64))
+    _, gr = mlp.loss_and_grad(pm, xh, th, True)
+    tol = GRAD_TOL[True]
+    assert all(_elementwise(gm[k], gr[k]) <= tol for k in gr)
+
+    planted = {}
+    w2 = gr["W2"].copy()
+    d = np.abs(w2 - w2.T)
+    i, j = np.unravel_index(np.argmax(d), d.shape)
+    w2[i, j], w2[j, i] = w2[j, i], w2[i, j]
+    planted["dW2 pair transposed"] = ("W2", w2)
+    b3 = gr["b3"].copy()
+    u = int(np.argmax(np.abs(np.diff(b3))))
+    b3[u] = b3[u + 1]
+    planted["db3 one unit off"] = ("b3", b3)
+    yh, cache = mlp.forward(pm, xh, True)
+    orig = mlp.silu_grad
+    monkeypatch.setattr(mlp, "silu_grad",
+                        lambda z: np.ones_like(z) if z is cache["z1"] else orig(z))
+    gbad = mlp.backward(pm, cache, (yh - th) / xh.shape[0], True)
+    monkeypatch.undo()
+    planted["no SiLU' in layer 1"] = ("W1", gbad["W1"])
+    for name, (k, bad) in planted.items():
+        assert _elementwise(gm[k], bad) > tol, name
 
 
 def test_adam_step_matches_reference():

@@ -6,12 +6,14 @@ cannot afford an allocation's synchronisation).  It reduces caller-owned
 device rows with partial sums kept in a fixed library array.  This test runs
 a solver through the normal entry points, hands rows 0 (a) and 1 (b) of its
 whole grid to bte_observe_noalloc twice in a row, and compares the drift
-velocity and norm with the solver's own trace at that step.  It lives in a
-file of its own, collected last.
+velocity and norm with the solver's own trace at that step and with the FP64
+oracle's reduction of the same rows.  It lives in a file of its own,
+collected last.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_1401_6047_gb300 import bte
 from paper_1401_6047_gb300 import workloads as W
 
@@ -32,6 +34,7 @@ def test_observe_noalloc_matches_solver_trace(prec):
     b1 = torch.tensor(b[1], dtype=dt, device="cuda")
     out = torch.zeros(2, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
+    v_or, n_or = oracle.observe(p, a, b)  # the same rows, reduced on the CPU in FP64
     tol = 1e-12
     for _ in range(2):  # two calls in a row share the fixed scratch array
         out.zero_()
@@ -40,6 +43,8 @@ def test_observe_noalloc_matches_solver_trace(prec):
         v, nr = out.tolist()
         assert abs(v - v_ref[0]) <= tol * max(1.0, abs(v_ref[0])), (v, v_ref[0])
         assert abs(nr - n_ref[0]) <= tol * max(1.0, abs(n_ref[0])), (nr, n_ref[0])
+        assert abs(v - v_or) <= tol * max(1.0, abs(v_or)), (v, v_or)
+        assert abs(nr - n_or) <= tol * max(1.0, abs(n_or)), (nr, n_or)
 
 
 def test_observe_noalloc_rejects_oversize():
