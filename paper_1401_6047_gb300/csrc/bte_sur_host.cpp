@@ -118,6 +118,7 @@ int forward(bte_sur* h, const float* x, const int* idx, long long row0, int nval
         a.Hout = layer == 0 ? h->H2 : h->H3;
         a.ldz = H;
         a.sZ = (long long)Bp * H;
+        a.err = h->err;
         KL(bte::sur::launch_gemm(a, false, false, bte::sur::EPI_FWD, h->M, h->stream));
     }
     return BTE_OK;
@@ -165,6 +166,7 @@ int backward(bte_sur* h, const float* x, const float* y, const int* idx, long lo
         gw.C = h->g + (layer == 1 ? h->off.W3 : h->off.W2);
         gw.ldc = H;
         gw.sC = h->pstride;
+        gw.err = h->err;
         KL(bte::sur::launch_gemm(gw, true, true, bte::sur::EPI_F32, h->M, h->stream));
         bte::sur::GemmArgs dh{};
         dh.A = dZ;
@@ -180,6 +182,7 @@ int backward(bte_sur* h, const float* x, const float* y, const int* idx, long lo
         dh.Dout = layer == 1 ? h->DZ2 : h->DZ1;
         dh.ldz = H;
         dh.sZ = sAct;
+        dh.err = h->err;
         KL(bte::sur::launch_gemm(dh, false, true, bte::sur::EPI_BWD, h->M, h->stream));
     }
     bte::sur::RedArgs r{};
@@ -473,6 +476,9 @@ int bte_sur_train(bte_sur* h, const int32_t* order, int32_t steps, int32_t batch
         if (loss)
             for (int m = 0; m < h->M; ++m) loss[(long long)s * h->M + m] = lh[m];
     }
+    int err = 0;
+    CU(cudaMemcpy(&err, h->err, sizeof err, cudaMemcpyDeviceToHost));
+    if (err) return fail(BTE_ETIMEOUT, "a bounded wait in a training GEMM gave up");
     return BTE_OK;
 }
 
@@ -505,6 +511,10 @@ int bte_sur_grad(bte_sur* h, const float* x, const float* t, int32_t n, float* g
         rc = fail(BTE_ECUDA, "loss copy failed");
     if (cudaStreamSynchronize(h->stream) != cudaSuccess && !rc) rc = fail(BTE_ECUDA, "sync failed");
     cudaFree(d);
+    int err = 0;
+    if (!rc && cudaMemcpy(&err, h->err, sizeof err, cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = fail(BTE_ECUDA, "error word read failed");
+    if (!rc && err) rc = fail(BTE_ETIMEOUT, "a bounded wait in a training GEMM gave up");
     return rc;
 }
 

@@ -56,7 +56,7 @@ enum Epi { EPI_FWD = 0, EPI_BWD = 1, EPI_F32 = 2 };
  *   EPI_BWD: Dout[m][n] = bf16(acc * silu'(Zin[m][n]))
  *   EPI_F32: C[m][n] = acc
  * A is stored [m][k] (a_kmajor = false) or [k][m]; B is stored [n][k]
- * (b_kmajor = false) or [k][n].  M, N multiples of 128; K of 32; every
+ * (b_kmajor = false) or [k][n].  M, N multiples of 128; K of 64; every
  * leading dimension a multiple of 8 elements, bases 16-byte aligned. */
 struct GemmArgs {
     const __nv_bfloat16* A;
@@ -73,6 +73,7 @@ struct GemmArgs {
     long long ldz, sZ; /* leading dimension / member stride of Z, Hout, Zin, Dout */
     float* C;
     long long ldc, sC;
+    int* err; /* set to 1 when a bounded wait gives up (may be null) */
 };
 
 /* Layer 1 (K = 5, FP32 FMAs): Z1 = W1 xh + b1, H1 = bf16(silu(Z1)), for

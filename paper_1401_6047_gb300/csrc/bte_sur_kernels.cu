@@ -2,26 +2,32 @@
  * bte_sur_kernels.cu -- CUDA kernels of the MLP surrogate (sm_103a).
  *
  * The two 256 x 256 hidden layers and their backward products run on the
- * BF16 tensor cores (mma.sync m16n8k16, FP32 accumulation) in one GEMM
- * kernel whose epilogue fuses the bias, the SiLU activation and its
- * derivative.  The thin layers (5 inputs, 2 outputs) are FP32 FMA kernels;
- * batch reductions are two-pass and deterministic; Adam keeps FP32 master
- * weights and refreshes the BF16 operand copies in the same pass.
+ * fifth-generation BF16 tensor cores (tcgen05.mma, FP32 accumulators in
+ * tensor memory) in one GEMM kernel whose epilogue fuses the bias, the SiLU
+ * activation and its derivative.  The thin layers (5 inputs, 2 outputs) are
+ * FP32 FMA kernels; batch reductions are two-pass and deterministic; Adam
+ * keeps FP32 master weights and refreshes the BF16 operand copies in the
+ * same pass.
  */
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "bte_device.cuh"
 #include "bte_sur_internal.h"
+#include "bte_tc.cuh"
 
 namespace bte {
 namespace sur {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 32;
-constexpr int kThreads = 256; /* 8 warps: 2 along M x 4 along N, warp tile 64 x 32 */
-constexpr int PAD = 8;        /* bf16 elements of row padding (16 bytes) */
-/* one stage: the larger of the [128][32+8] and [32][128+8] tile shapes */
-constexpr int kTileElems = (BM * (BK + PAD) > BK * (BM + PAD)) ? BM * (BK + PAD) : BK * (BM + PAD);
+/* tcgen05 GEMM tile: 128 x 128 outputs per CTA (one MMA of M = N = 128
+ * per 16 of K), K in stages of 64, two stages in shared memory. */
+constexpr int GM = 128, GN = 128, GK = 64;
+constexpr int kGThreads = 256; /* 8 warps: two per tensor-memory lane quadrant */
+constexpr uint32_t kGTileBytes = (uint32_t)GM * GK * 2; /* 16 KB per operand tile */
+constexpr uint32_t kGCore = 128;                        /* one 8 x 8 core matrix */
+constexpr uint32_t kGGroup = (GK / 8) * kGCore;         /* 1024: next 8-row group */
+constexpr size_t kGSmem = 4 * (size_t)kGTileBytes + 64 + 1024; /* 2 stages x (A, B), barriers, align */
 
 /* sigmoid(z) = 1 / (1 + exp(-z)) with the fast exponential and reciprocal
  * (relative error ~1e-7, so the bfloat16 rounding that follows matches an
@@ -33,158 +39,199 @@ __device__ __forceinline__ float silu_grad_f(float z) {
     return s * (1.0f + z * (1.0f - s));
 }
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+/* byte offset of element (r, k) of a [128][64] K-major stage tile in the
+ * tensor cores' canonical layout without swizzle (8 x 8 core matrices of
+ * 128 contiguous bytes, K-adjacent core matrices 128 bytes apart, 8-row
+ * groups 1024 bytes apart) */
+__device__ __forceinline__ uint32_t gcanon(int r, int k) {
+    return (uint32_t)(((r >> 3) * (GK / 8) + (k >> 3)) * kGCore + (r & 7) * 16 + (k & 7) * 2);
 }
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_addr(p)));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_addr(p)));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-/* Copies one 128 x 32 operand tile into shared memory.  kmajor = false:
- * global [row][k] (row = m or n), shared [128][32+PAD]; kmajor = true:
- * global [k][row], shared [32][128+PAD]. */
-template <bool KMAJOR>
-__device__ __forceinline__ void load_tile(__nv_bfloat16* s, const __nv_bfloat16* g, long long ld,
-                                          int row0, int k0) {
+/* One 128-row x 64-k operand tile into shared memory (canonical layout).
+ * K-major source ([row][k], leading dimension ld): 1024 chunks of 8 k, four
+ * per thread; a quarter-warp writes one core matrix (8 rows of one chunk
+ * column, 128 contiguous bytes).  MN-major source ([k][row]): 128 blocks
+ * of 8 k x 8 rows, one per thread of `first` .. `first + 127`, read as
+ * eight 16-byte rows and transposed in registers (byte permutes) into the
+ * eight 16-byte rows of one core matrix. */
+template <bool MN>
+__device__ __forceinline__ void load_stage(unsigned char* s, const __nv_bfloat16* g, long long ld,
+                                           int row0, int k0, int first) {
     const int t = threadIdx.x;
+    if constexpr (!MN) {
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int c = t + q * kThreads; /* 512 chunks of 8 elements */
-        if (!KMAJOR) {
-            const int r = c >> 2, kc = (c & 3) * 8;
-            cp_async16(s + r * (BK + PAD) + kc, g + (long long)(row0 + r) * ld + k0 + kc);
-        } else {
-            const int k = c >> 4, rc = (c & 15) * 8;
-            cp_async16(s + k * (BM + PAD) + rc, g + (long long)(k0 + k) * ld + row0 + rc);
+        for (int q = 0; q < 4; ++q) {
+            const int c = t + q * kGThreads;
+            const int r = (c & 7) + 8 * (c >> 6), kc = (c >> 3) & 7;
+            const uint4 v =
+                __ldg(reinterpret_cast<const uint4*>(g + (long long)(row0 + r) * ld + k0 + kc * 8));
+            *reinterpret_cast<uint4*>(s + gcanon(r, kc * 8)) = v;
+        }
+    } else {
+        const int b = t - first;
+        if (b < 0 || b >= 128) return;
+        const int rb = b & 15, kb = b >> 4; /* 16 row blocks x 8 k blocks */
+        uint32_t w[8][4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(
+                g + (long long)(k0 + kb * 8 + i) * ld + row0 + rb * 8));
+            w[i][0] = v.x;
+            w[i][1] = v.y;
+            w[i][2] = v.z;
+            w[i][3] = v.w;
+        }
+        unsigned char* dst = s + (uint32_t)((rb * (GK / 8) + kb) * kGCore);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            /* row j of the core matrix: element j of input rows 0..7 */
+            const uint32_t sel = (j & 1) ? 0x7632u : 0x5410u;
+            uint4 o;
+            o.x = __byte_perm(w[0][j >> 1], w[1][j >> 1], sel);
+            o.y = __byte_perm(w[2][j >> 1], w[3][j >> 1], sel);
+            o.z = __byte_perm(w[4][j >> 1], w[5][j >> 1], sel);
+            o.w = __byte_perm(w[6][j >> 1], w[7][j >> 1], sel);
+            *reinterpret_cast<uint4*>(dst + j * 16) = o;
         }
     }
 }
 
-template <bool AK, bool BKM, int EPI>
-__global__ void __launch_bounds__(kThreads) gemm_kernel(GemmArgs a) {
-    __shared__ __align__(128) __nv_bfloat16 sA[2][kTileElems];
-    __shared__ __align__(128) __nv_bfloat16 sB[2][kTileElems];
+/* C = A B^T on the tensor cores (see GemmArgs).  One CTA per 128 x 128
+ * output tile of one member (blockIdx.z).  K advances in stages of 64: the
+ * CTA's threads fill stage s (global loads, transposed where the operand
+ * is stored MN-major) while the tensor cores still work on the other
+ * stage; one thread issues the four M = N = 128, K = 16 MMAs of a stage
+ * into 128 columns of tensor memory and commits them to the stage's
+ * mbarrier, which tells the threads when they may refill it.  The
+ * epilogue reads the accumulators back with tcgen05.ld (warp w: lanes
+ * 32 (w mod 4) .., columns 64 (w / 4) ..).  Every wait is bounded; a wait
+ * that gives up sets the error word, and the CTA still frees its tensor
+ * memory before it exits. */
+template <bool AMN, bool BMN, int EPI>
+__global__ void __launch_bounds__(kGThreads) gemm_tc_kernel(GemmArgs a) {
+    extern __shared__ unsigned char gsm_raw[];
+    unsigned char* gsm = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~(uintptr_t)1023);
+    /* stage s: A tile at s * 16 KB, B tile at (2 + s) * 16 KB; barrier s at 64 KB + 8 s */
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gsm + 4 * kGTileBytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gsm + 4 * kGTileBytes + 32);
+    const uint32_t bar0 = dev::smem_u32(bars);
+
     const int mem = blockIdx.z;
     const __nv_bfloat16* A = a.A + mem * a.sA;
     const __nv_bfloat16* B = a.B + mem * a.sB;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
+    const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    bool ok = true;
 
-    float acc[4][4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
+    if (tid == 0) {
+        dev::mbar_init(bar0, 1);
+        dev::mbar_init(bar0 + 8, 1);
+        dev::fence_proxy_async_smem();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         dev::smem_u32(tmem_slot)),
+                     "r"(GN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    constexpr uint32_t idesc = tc::instr_desc(GM, GN);
 
-    const int nk = a.K / BK;
-    load_tile<AK>(sA[0], A, a.lda, m0, 0);
-    load_tile<BKM>(sB[0], B, a.ldb, n0, 0);
-    cp_async_commit();
+    const int nk = a.K / GK;
     for (int kt = 0; kt < nk; ++kt) {
         const int st = kt & 1;
-        if (kt + 1 < nk) {
-            load_tile<AK>(sA[st ^ 1], A, a.lda, m0, (kt + 1) * BK);
-            load_tile<BKM>(sB[st ^ 1], B, a.ldb, n0, (kt + 1) * BK);
-        }
-        cp_async_commit();
-        cp_async_wait<1>();
+        unsigned char* sA = gsm + st * kGTileBytes;
+        unsigned char* sB = gsm + (2 + st) * kGTileBytes;
+        const uint32_t bar = bar0 + 8 * st;
+        /* the MMAs that read this stage two rounds ago are complete */
+        if (kt >= 2 && !dev::mbar_wait(bar, (uint32_t)(((kt - 2) >> 1) & 1))) ok = false;
+        if (__syncthreads_or(!ok)) break;
+        load_stage<AMN>(sA, A, a.lda, m0, kt * GK, 0);
+        load_stage<BMN>(sB, B, a.ldb, n0, kt * GK, AMN ? 128 : 0);
+        /* generic-proxy writes -> visible to the tensor cores */
+        dev::fence_proxy_async_smem();
         __syncthreads();
-        const __nv_bfloat16* tA = sA[st];
-        const __nv_bfloat16* tB = sB[st];
+        if (tid == 0) {
+            tc::tc_fence_after();
+            const uint32_t aA = dev::smem_u32(sA), aB = dev::smem_u32(sB);
 #pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t af[4][4];
-            const int j = lane >> 3, r = lane & 7;
-#pragma unroll
-            for (int mi = 0; mi < 4; ++mi) {
-                const int mb = wm + mi * 16;
-                if (!AK) {
-                    ldsm_x4(af[mi], tA + (mb + (lane & 15)) * (BK + PAD) + kk + (lane >> 4) * 8);
-                } else {
-                    ldsm_x4_t(af[mi], tA + (kk + (j >> 1) * 8 + r) * (BM + PAD) + mb + (j & 1) * 8);
-                }
+            for (int ks = 0; ks < GK / 16; ++ks) {
+                const uint64_t ad = tc::smem_desc(aA + ks * 2 * kGCore, kGCore, kGGroup);
+                const uint64_t bd = tc::smem_desc(aB + ks * 2 * kGCore, kGCore, kGGroup);
+                tc::tc_mma(tmem, ad, bd, idesc, (kt > 0 || ks > 0) ? 1u : 0u);
             }
-            uint32_t bf[4][2];
-#pragma unroll
-            for (int ni = 0; ni < 4; ni += 2) {
-                const int nb = wn + ni * 8;
-                uint32_t t4[4];
-                if (!BKM) {
-                    ldsm_x4(t4, tB + (nb + (j >> 1) * 8 + r) * (BK + PAD) + kk + (j & 1) * 8);
-                } else {
-                    ldsm_x4_t(t4, tB + (kk + (j & 1) * 8 + r) * (BN + PAD) + nb + (j >> 1) * 8);
-                }
-                bf[ni][0] = t4[0];
-                bf[ni][1] = t4[1];
-                bf[ni + 1][0] = t4[2];
-                bf[ni + 1][1] = t4[3];
-            }
-#pragma unroll
-            for (int mi = 0; mi < 4; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bf[ni][0], bf[ni][1]);
+            tc::tc_commit(bar);
         }
-        __syncthreads();
     }
+    /* the last commit covers every MMA issued before it */
+    if (ok && nk > 0 && !dev::mbar_wait(bar0 + 8 * ((nk - 1) & 1), (uint32_t)(((nk - 1) >> 1) & 1)))
+        ok = false;
+    if (ok && nk > 1 && !dev::mbar_wait(bar0 + 8 * (nk & 1), (uint32_t)(((nk - 2) >> 1) & 1)))
+        ok = false;
+    tc::tc_fence_after();
 
-    /* epilogue: thread holds rows g, g+8 and columns 2q, 2q+1 of each 16 x 8 tile */
-    const int g = lane >> 2, q = lane & 3;
+    if (ok) {
+        const int sub = warp & 3, half = warp >> 2;
+        const int row = m0 + sub * 32 + lane;
+#pragma unroll 1
+        for (int cb = 0; cb < GN / 2; cb += 32) {
+            const int cl = half * (GN / 2) + cb; /* column within the tile */
+            float v[32];
+            tc::tc_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)cl, v);
+            const int col = n0 + cl;
+            if (EPI == EPI_FWD) {
+                const float* bias = a.bias + mem * a.sBias + col;
+                const long long o = mem * a.sZ + (long long)row * a.ldz + col;
 #pragma unroll
-    for (int mi = 0; mi < 4; ++mi)
+                for (int c8 = 0; c8 < 32; c8 += 8) {
+                    float z[8];
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
+                    for (int e = 0; e < 8; ++e) z[e] = v[c8 + e] + bias[c8 + e];
+                    if (a.Z) {
+                        *reinterpret_cast<float4*>(a.Z + o + c8) = make_float4(z[0], z[1], z[2], z[3]);
+                        *reinterpret_cast<float4*>(a.Z + o + c8 + 4) = make_float4(z[4], z[5], z[6], z[7]);
+                    }
+                    __nv_bfloat162 pk[4];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int row = m0 + wm + mi * 16 + g + 8 * h;
-                const int col = n0 + wn + ni * 8 + 2 * q;
-                const float v0 = acc[mi][ni][2 * h], v1 = acc[mi][ni][2 * h + 1];
-                if (EPI == EPI_FWD) {
-                    const float* bias = a.bias + mem * a.sBias;
-                    const float z0 = v0 + bias[col], z1 = v1 + bias[col + 1];
-                    const long long o = mem * a.sZ + (long long)row * a.ldz + col;
-                    if (a.Z) *reinterpret_cast<float2*>(a.Z + o) = make_float2(z0, z1);
-                    *reinterpret_cast<__nv_bfloat162*>(a.Hout + o) =
-                        __floats2bfloat162_rn(silu_f(z0), silu_f(z1));
-                } else if (EPI == EPI_BWD) {
-                    const long long o = mem * a.sZ + (long long)row * a.ldz + col;
-                    const float2 z = *reinterpret_cast<const float2*>(a.Zin + o);
-                    *reinterpret_cast<__nv_bfloat162*>(a.Dout + o) =
-                        __floats2bfloat162_rn(v0 * silu_grad_f(z.x), v1 * silu_grad_f(z.y));
-                } else {
-                    const long long o = mem * a.sC + (long long)row * a.ldc + col;
-                    *reinterpret_cast<float2*>(a.C + o) = make_float2(v0, v1);
+                    for (int e = 0; e < 4; ++e)
+                        pk[e] = __floats2bfloat162_rn(silu_f(z[2 * e]), silu_f(z[2 * e + 1]));
+                    *reinterpret_cast<uint4*>(a.Hout + o + c8) = *reinterpret_cast<const uint4*>(pk);
                 }
+            } else if (EPI == EPI_BWD) {
+                const long long o = mem * a.sZ + (long long)row * a.ldz + col;
+#pragma unroll
+                for (int c8 = 0; c8 < 32; c8 += 8) {
+                    const float4 z0 = *reinterpret_cast<const float4*>(a.Zin + o + c8);
+                    const float4 z1 = *reinterpret_cast<const float4*>(a.Zin + o + c8 + 4);
+                    const float z[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+                    __nv_bfloat162 pk[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        pk[e] = __floats2bfloat162_rn(v[c8 + 2 * e] * silu_grad_f(z[2 * e]),
+                                                      v[c8 + 2 * e + 1] * silu_grad_f(z[2 * e + 1]));
+                    *reinterpret_cast<uint4*>(a.Dout + o + c8) = *reinterpret_cast<const uint4*>(pk);
+                }
+            } else {
+                const long long o = mem * a.sC + (long long)row * a.ldc + col;
+#pragma unroll
+                for (int c4 = 0; c4 < 32; c4 += 4)
+                    *reinterpret_cast<float4*>(a.C + o + c4) =
+                        make_float4(v[c4], v[c4 + 1], v[c4 + 2], v[c4 + 3]);
             }
+        }
+    }
+    if (!ok && tid == 0 && a.err) atomicExch(a.err, 1);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GN)
+                     : "memory");
 }
 
 __device__ __forceinline__ void load_xh(const float* x, const int* idx, long long row0, int r,
@@ -426,21 +473,26 @@ int ok_or(cudaError_t e) { return e == cudaSuccess ? 0 : (int)e; }
 
 int reduce_count(int H) { return red_count(H); }
 
+template <bool AMN, bool BMN, int EPI>
+static int launch_tc(const GemmArgs& a, int members, cudaStream_t s) {
+    const void* fn = reinterpret_cast<const void*>(&gemm_tc_kernel<AMN, BMN, EPI>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGSmem);
+    if (e != cudaSuccess) return (int)e;
+    const dim3 grid(a.N / GN, a.M / GM, members);
+    gemm_tc_kernel<AMN, BMN, EPI><<<grid, kGThreads, kGSmem, s>>>(a);
+    return ok_or(cudaGetLastError());
+}
+
 int launch_gemm(const GemmArgs& a, bool a_kmajor, bool b_kmajor, int epi, int members,
                 void* stream) {
-    const dim3 grid(a.N / BN, a.M / BM, members);
-    cudaStream_t s = (cudaStream_t)stream;
-    if (!a_kmajor && !b_kmajor && epi == EPI_FWD)
-        gemm_kernel<false, false, EPI_FWD><<<grid, kThreads, 0, s>>>(a);
-    else if (!a_kmajor && b_kmajor && epi == EPI_BWD)
-        gemm_kernel<false, true, EPI_BWD><<<grid, kThreads, 0, s>>>(a);
-    else if (a_kmajor && b_kmajor && epi == EPI_F32)
-        gemm_kernel<true, true, EPI_F32><<<grid, kThreads, 0, s>>>(a);
-    else if (!a_kmajor && !b_kmajor && epi == EPI_F32)
-        gemm_kernel<false, false, EPI_F32><<<grid, kThreads, 0, s>>>(a);
-    else
+    if (a.M % GM || a.N % GN || a.K % GK || a.M <= 0 || a.N <= 0 || a.K <= 0)
         return (int)cudaErrorInvalidValue;
-    return ok_or(cudaGetLastError());
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!a_kmajor && !b_kmajor && epi == EPI_FWD) return launch_tc<false, false, EPI_FWD>(a, members, s);
+    if (!a_kmajor && b_kmajor && epi == EPI_BWD) return launch_tc<false, true, EPI_BWD>(a, members, s);
+    if (a_kmajor && b_kmajor && epi == EPI_F32) return launch_tc<true, true, EPI_F32>(a, members, s);
+    if (!a_kmajor && !b_kmajor && epi == EPI_F32) return launch_tc<false, false, EPI_F32>(a, members, s);
+    return (int)cudaErrorInvalidValue;
 }
 
 int launch_l1(const L1Args& a, int members, void* stream) {
