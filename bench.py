@@ -715,15 +715,8 @@ def run_sweep(args, emit: bool = True):
                        "max_batch_bytes": max_bytes, "points_not_ok": bad,
                        "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"points split over {world} rank(s)"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "peak_source": peak_kind + " hbm_gbs",
-                         "kernel": "resident_kernel (on-chip tier) + fused_step_kernel (streamed tier)",
-                         "on_chip_share_of_cell_updates": cu_on / cu if cu else 0.0,
-                         "note": "algorithmic bytes (32 B FP32 / 64 B FP64 per cell-update) "
-                                 "over the whole batch solve, against HBM for comparison with the "
-                                 "streamed tier; the on-chip tier keeps the state in shared memory "
-                                 "and moves no HBM bytes per step"},
+            "roofline": sweep_roofline(cu * world * args.steps / secs, achieved, peak, peak_kind,
+                                       cu_on / cu if cu else 0.0, elem, clk),
             "cpu_baseline": cpu, "single_instance_gpu": single, "e2e": e2e, "tuned": tuned,
             "gpu_launches": launches * args.steps, "clocks": clk,
         }
@@ -733,6 +726,42 @@ def run_sweep(args, emit: bool = True):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+# FP32 lane operations (multiply, add, fused multiply-add) of one cell-update,
+# both grids: 24 per cell of a half-step in the Crank-Nicolson update and 2
+# for the phi_y differences of the row it contributes (the reciprocal of the
+# denominator runs on the special-function unit and is not counted)
+FP32_OPS_PER_CELL_UPDATE = 52
+
+
+def sweep_roofline(cell_updates_per_s, hbm_achieved, hbm_peak, peak_kind, on_chip_share, elem, clk):
+    """Roof of the batched sweep.  When the on-chip tier carries (nearly)
+    every cell-update the state never leaves shared memory, so the bound is
+    the FP32 arithmetic: 152 SMs x 128 FP32 lanes x the SM clock (the
+    maximum, 2070 MHz, when no clock sample is at hand) against
+    FP32_OPS_PER_CELL_UPDATE lane operations per cell-update.  Otherwise
+    the HBM roof of the streamed tier with 32 / 64 B per cell-update."""
+    if elem == 4 and on_chip_share >= 0.99:
+        mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+        peak = 152 * 128 * mhz * 1e6 / 1e12  # Tops/s
+        achieved = cell_updates_per_s * FP32_OPS_PER_CELL_UPDATE / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "T FP32 lane-ops/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz (one lane operation per "
+                               f"lane and clock; FMA counted once)",
+                "ops_per_cell_update": FP32_OPS_PER_CELL_UPDATE,
+                "kernel": "resident_kernel (on-chip tier)",
+                "on_chip_share_of_cell_updates": on_chip_share,
+                "hbm_equivalent": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm_peak,
+                                   "note": "algorithmic bytes of the streamed form, for comparison"}}
+    return {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": hbm_achieved / hbm_peak, "traffic": None,
+            "peak_source": peak_kind + " hbm_gbs",
+            "kernel": "resident_kernel (on-chip tier) + fused_step_kernel (streamed tier)",
+            "on_chip_share_of_cell_updates": on_chip_share,
+            "note": "algorithmic bytes (32 B FP32 / 64 B FP64 per cell-update) over the whole "
+                    "batch solve"}
 
 
 def run_sweep_reference(args):
@@ -772,9 +801,10 @@ def run_sweep_reference(args):
 
 
 SUR_DESC = ("learned surrogate: 8-member ensemble of MLP 5-256-256-256-2 (SiLU), BF16 tensor-core "
-            "layers with FP32 accumulation, trained on 32,768 sweep-box points solved by the "
-            "batched solver; inference on 1M seeded points (seed 2014) of the same box, solver "
-            "fallback where the ensemble std exceeds 1e-3")
+            "layers with FP32 accumulation, trained on 200,000 sweep-box points (seed 6047) solved "
+            "by the batched solver, judged on 10,240 held-out points (seed 2015); inference on 1M "
+            "seeded points (seed 2014) of the same box, solver fallback where the ensemble std "
+            "exceeds 1e-3")
 
 
 def sur_flops_per_point(members=8, H=256):

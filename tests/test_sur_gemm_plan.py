@@ -8,7 +8,8 @@ global read stays inside its operand, every shared-memory write inside its
 16 KB stage tile, every tile byte is written exactly once, and the product
 decoded from the descriptors equals A B^T for all three operand layouts the
 training pass uses.  Mirrors the arithmetic of gemm_tc_kernel and
-load_stage in csrc/bte_sur_kernels.cu."""
+load_stage in csrc/bte_sur_kernels.cu; the last test does the same for the
+inference kernel's operand and weight-chunk layouts (csrc/bte_sur_tc.cu)."""
 import numpy as np
 import pytest
 
@@ -100,3 +101,52 @@ def test_stage_fill_and_descriptors_give_a_times_b_transposed(amn, bmn):
                 acc += decode(ia, GM) @ decode(ib, GN).T
             C[m0:m0 + GM, n0:n0 + GN] = acc
     assert np.array_equal(C, A @ B.T)
+
+
+def test_inference_weight_chunks_and_operand_decode_through_descriptors():
+    """Inference kernel (csrc/bte_sur_tc.cu): W2/W3 stored per 64-input
+    K-chunk ([256 outputs][64 inputs], 8-row groups 1024 bytes apart) and
+    h stored [128 rows][256] (8-row groups 4096 bytes apart).  Decoding the
+    MMAs of chunk c, weight half hh, K-step k4 through their descriptors
+    (start = slot + hh * 16 KB + k4 * 256 for the weights, h + (4 c + k4) *
+    256 for the operand; K-adjacent core matrices 128 bytes apart) gives
+    back W[128 hh + n][64 c + 16 k4 + kk] and h[r][64 c + 16 k4 + kk]."""
+    def wcanon(n, k):
+        return ((n >> 3) * 8 + (k >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2
+
+    def canon(r, k):
+        return ((r >> 3) * 32 + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2
+
+    rng = np.random.default_rng(3)
+    W = rng.integers(-1000, 1000, size=(256, 256))
+    h = rng.integers(-1000, 1000, size=(128, 256))
+    chunks = []
+    for c in range(4):
+        img = np.full(256 * 64, -10**9, dtype=np.int64)
+        for n in range(256):
+            for k in range(64):
+                off = wcanon(n, k)
+                assert 0 <= off < 32768 and off % 2 == 0
+                img[off // 2] = W[n, 64 * c + k]
+        assert np.all(img >= -1000), "every byte of the chunk written"
+        chunks.append(img)
+    himg = np.full(128 * 256, -10**9, dtype=np.int64)
+    for r in range(128):
+        for k in range(256):
+            himg[canon(r, k) // 2] = h[r, k]
+    assert np.all(himg >= -1000), "every byte of h written"
+    acc = np.zeros((128, 256), dtype=np.int64)
+    for c in range(4):
+        for hh in range(2):
+            for k4 in range(4):
+                ks = 4 * c + k4
+                a = np.zeros((128, 16), dtype=np.int64)
+                b = np.zeros((128, 16), dtype=np.int64)
+                for r in range(128):
+                    for kk in range(16):
+                        a[r, kk] = himg[(ks * 256 + (kk >> 3) * 128 + (r >> 3) * 4096 + (r & 7) * 16
+                                         + (kk & 7) * 2) // 2]
+                        b[r, kk] = chunks[c][(hh * 16384 + k4 * 256 + (kk >> 3) * 128 + (r >> 3) * 1024
+                                              + (r & 7) * 16 + (kk & 7) * 2) // 2]
+                acc[:, 128 * hh:128 * hh + 128] += a @ b.T
+    assert np.array_equal(acc, h @ W.T)
