@@ -143,7 +143,14 @@ typedef struct {
                             grids measured (401 x 4001 FP32: 20.9 against
                             17.4 us per step).
                             0: one fused step kernel launch per step.      */
-    int32_t reserved;    /* must be 0                                      */
+    int32_t walk;        /* order in which one-step launches walk the
+                            harmonic rows of a work item: 0 automatic
+                            (alternate when the ping-pong state exceeds 96
+                            MB, so that each step starts with the rows the
+                            step before wrote last, which L2 still holds;
+                            upward otherwise), 1 upward every step, 2
+                            alternate every step.  The results are the same
+                            bits in every order.                           */
 } bte_tuning;
 
 typedef struct bte_handle bte_handle;
@@ -281,7 +288,8 @@ typedef struct bte_batch_opts {
     void* stream;            /* cudaStream_t to queue on (NULL: a private stream)     */
     int32_t resident_smem;   /* shared memory per CTA for on-chip points, bytes
                                 (0: 232,448, the most a CTA may have)                */
-    int32_t reserved;        /* must be 0                                             */
+    int32_t walk;            /* row-walk order of the streamed tier, as
+                                bte_tuning.walk (for the batch's total state)        */
 } bte_batch_opts;
 
 /* Full solve (Sec. 3 scheme from the Sec. 2 initial state, window averages

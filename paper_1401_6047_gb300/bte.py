@@ -52,7 +52,7 @@ class bte_obs(ctypes.Structure):
 class bte_tuning(ctypes.Structure):
     _fields_ = [("tile_m", ctypes.c_int32), ("chunk_n", ctypes.c_int32),
                 ("graph_steps", ctypes.c_int32), ("vec", ctypes.c_int32),
-                ("resident", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("resident", ctypes.c_int32), ("walk", ctypes.c_int32)]
 
 
 class bte_batch_opts(ctypes.Structure):
@@ -60,7 +60,7 @@ class bte_batch_opts(ctypes.Structure):
                 ("graph_steps", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("resident", ctypes.c_int32), ("max_batch_bytes", ctypes.c_int64),
                 ("stream", ctypes.c_void_p), ("resident_smem", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("walk", ctypes.c_int32)]
 
 
 _lib = None
@@ -147,10 +147,10 @@ def to_params(p) -> bte_params:
     return s
 
 
-def _tuning(tile_m=0, chunk_n=0, graph_steps=0, vec=0, resident=0):
+def _tuning(tile_m=0, chunk_n=0, graph_steps=0, vec=0, resident=0, walk=0):
     t = bte_tuning()
     t.tile_m, t.chunk_n, t.graph_steps, t.vec = int(tile_m), int(chunk_n), int(graph_steps), int(vec)
-    t.resident, t.reserved = int(resident), 0
+    t.resident, t.walk = int(resident), int(walk)
     return t
 
 
@@ -228,11 +228,11 @@ class Solver:
 
     def __init__(self, p, stream: int = 0, tile_m: int = 0, chunk_n: int = 0,
                  graph_steps: int = 0, workspace: int = 0, workspace_bytes: int = 0,
-                 vec: int = 0, resident: int = 0):
+                 vec: int = 0, resident: int = 0, walk: int = 0):
         self._lib = lib()
         self.params = to_params(p)
         self._h = ctypes.c_void_p()
-        t = _tuning(tile_m, chunk_n, graph_steps, vec, resident)
+        t = _tuning(tile_m, chunk_n, graph_steps, vec, resident, walk)
         _check(self._lib.bte_create_ex(ctypes.byref(self.params), ctypes.c_void_p(stream or None),
                                        ctypes.byref(t), ctypes.c_void_p(workspace or None),
                                        int(workspace_bytes), ctypes.byref(self._h)))
@@ -318,11 +318,11 @@ def _obs(o: bte_obs) -> Observables:
 
 
 def _batch_opts(tile_m=0, chunk_n=0, vec=0, graph_steps=0, max_batch=0, max_batch_bytes=0,
-                stream=0, resident=0, resident_smem=0):
+                stream=0, resident=0, resident_smem=0, walk=0):
     o = bte_batch_opts()
     o.tile_m, o.chunk_n, o.vec, o.graph_steps = int(tile_m), int(chunk_n), int(vec), int(graph_steps)
     o.max_batch, o.resident, o.max_batch_bytes = int(max_batch), int(resident), int(max_batch_bytes)
-    o.resident_smem, o.reserved = int(resident_smem), 0
+    o.resident_smem, o.walk = int(resident_smem), int(walk)
     o.stream = ctypes.c_void_p(stream or None)
     return o
 
@@ -360,7 +360,7 @@ def batch_tune(points, sample: int = 16, steps: int = 2000, **opts):
 
 def batch_run(points, tile_m: int = 0, chunk_n: int = 0, vec: int = 0, graph_steps: int = 0,
               max_batch: int = 0, max_batch_bytes: int = 0, stream: int = 0,
-              resident: int = 0, resident_smem: int = 0,
+              resident: int = 0, resident_smem: int = 0, walk: int = 0,
               check: bool = True) -> list[Observables]:
     """Full solves of many parameter points (``bte_batch_run``); returns one
     ``Observables`` per point, in order.  ``resident``: 0 on chip where a
@@ -371,7 +371,7 @@ def batch_run(points, tile_m: int = 0, chunk_n: int = 0, vec: int = 0, graph_ste
     arr = (bte_params * max(n, 1))(*[to_params(q) for q in pts])
     out = (bte_obs * max(n, 1))()
     o = _batch_opts(tile_m, chunk_n, vec, graph_steps, max_batch, max_batch_bytes, stream, resident,
-                    resident_smem)
+                    resident_smem, walk)
     rc = lib().bte_batch_run(arr, n, out, ctypes.byref(o))
     if check:
         _check(rc)

@@ -179,6 +179,7 @@ struct Layout {
     int G, H, pitch, tile_m, chunk_n, vec, ts, ntx, nty;
     int resC;                 /* on-chip mode: CTAs of the cluster, 0 = streamed */
     bool persist;             /* persistent mode: one launch per call, grid barriers */
+    int walk;                 /* tuning.walk: 0 automatic, 1 upward, 2 alternate */
     size_t res_smem, res_arrays; /* its shared memory per CTA, and the arrays' part */
     size_t elem;
     size_t off_state[8];
@@ -197,7 +198,7 @@ constexpr size_t kResBytes = 1024;
 constexpr int kResThreads = 512; /* threads per CTA of the on-chip kernel */
 
 int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L) {
-    if (t && t->reserved) return fail(BTE_EINVAL, "tuning.reserved must be 0");
+    if (t && (t->walk < 0 || t->walk > 2)) return fail(BTE_EINVAL, "tuning.walk must be 0, 1 or 2");
     if (t && (t->resident < 0 || t->resident > 2))
         return fail(BTE_EINVAL, "tuning.resident must be 0, 1 or 2");
     int rc = pick_tile(p, t, L.tile_m, L.chunk_n, L.vec);
@@ -207,6 +208,7 @@ int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L
     L.resC = 0;
     L.res_smem = L.res_arrays = 0;
     L.persist = t && t->resident == 2;
+    L.walk = t ? t->walk : 0;
     if (t && t->resident == 1) {
         const int N1 = p->n_max + 1;
         for (int C = 16; C >= 1; C /= 2) {
@@ -350,6 +352,8 @@ bte::StepArgs<T> step_args(const bte_handle* h) {
     a.nty = L.nty;
     a.vec = L.vec;
     a.grid = h->grid[L.ts];
+    a.alt = L.walk == 2 ||
+            (L.walk == 0 && 8 * L.elem * (size_t)(h->p.n_max + 1) * (size_t)L.pitch > bte::kAltStateBytes);
     const double dt = h->tg.dt_eff;
     a.h = (T)dt;
     a.hh = (T)(0.5 * dt);
@@ -704,7 +708,7 @@ constexpr int kAcc = 8; /* per-instance accumulators, see BatchInst::acc */
  * or (resident) on chip, one cluster of pts[i].resC CTAs per point. */
 template <typename T>
 int run_batch(const bte_params* p, std::vector<BatchPoint>& pts, size_t first, size_t last,
-              int tile, int chunk, int vec, int graph_len, bool resident, cudaStream_t st,
+              int tile, int chunk, int vec, int graph_len, bool resident, int walk, cudaStream_t st,
               cudaStream_t cap, bte_obs* out) {
     const int elem = (int)sizeof(T);
     const int G = 128 / elem, Hp = 32 / elem;
@@ -888,6 +892,7 @@ int run_batch(const bte_params* p, std::vector<BatchPoint>& pts, size_t first, s
     ba.tile_m = tile;
     ba.chunk_n = chunk;
     ba.vec = vec;
+    ba.alt = walk == 2 || (walk == 0 && states_end > bte::kAltStateBytes);
     if (resident) {
         /* on chip: one persistent launch per cluster size, all launches
          * concurrent (each on its own stream, so the CTAs that one launch
@@ -1129,7 +1134,7 @@ int batch_prepare(const bte_params* p, int32_t n, const bte_batch_opts* opts,
     if (mode < 0 || mode > 2) return fail(BTE_EINVAL, "resident must be 0, 1 or 2");
     const long long budget = (opts && opts->resident_smem > 0) ? opts->resident_smem : 232448;
     if (budget > 232448) return fail(BTE_EINVAL, "resident_smem above 232,448 bytes");
-    if (opts && opts->reserved) return fail(BTE_EINVAL, "reserved field must be 0");
+    if (opts && (opts->walk < 0 || opts->walk > 2)) return fail(BTE_EINVAL, "walk must be 0, 1 or 2");
     for (auto& b : pts) {
         b.ntx = (b.M1 + tile - 1) / tile;
         b.nty = (b.N1 + chunk - 1) / chunk;
@@ -1223,8 +1228,9 @@ int bte_batch_run(const bte_params* p, int32_t n, bte_obs* out, const bte_batch_
             ++last;
         }
         const bool res = resC > 0;
-        const int rc = fp64 ? run_batch<double>(p, pts, first, last, tile, chunk, vec, graph_len, res, st, cap, out)
-                            : run_batch<float>(p, pts, first, last, tile, chunk, vec, graph_len, res, st, cap, out);
+        const int walk = opts ? opts->walk : 0;
+        const int rc = fp64 ? run_batch<double>(p, pts, first, last, tile, chunk, vec, graph_len, res, walk, st, cap, out)
+                            : run_batch<float>(p, pts, first, last, tile, chunk, vec, graph_len, res, walk, st, cap, out);
         if (rc == BTE_ECUDA || rc == BTE_ENOMEM) {
             worst = rc;
             break;

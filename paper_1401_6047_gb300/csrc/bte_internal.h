@@ -30,6 +30,12 @@ struct Cols {
     static constexpr int H = 16 / (int)sizeof(T);
 };
 
+/* Ping-pong state above this many bytes does not stay in L2 (129 MB on a
+ * GB300) from one step to the next: the step kernel then alternates the
+ * direction of its row walks, so that each step starts with the rows the
+ * step before wrote last. */
+constexpr size_t kAltStateBytes = 96ull << 20;
+
 /* Arguments of the fused step kernel (one leap-frog step). */
 template <typename T>
 struct StepArgs {
@@ -62,6 +68,8 @@ struct StepArgs {
     int tile_m, chunk_n, ntx, nty;
     int vec;              /* phi_y columns per compute thread (2 or 4)         */
     int grid;             /* persistent CTAs; items are ntx * nty              */
+    int alt;              /* 1: one-step launches alternate the row-walk
+                             direction (a state larger than L2)              */
     T h, hh, nu, xi;      /* dt, dt/2, 1 + dt/2, 1 - dt/2                        */
     double vscale, nscale;/* pi sqrt(alpha) dphi, 2 pi sqrt(alpha) dphi          */
 };
@@ -107,6 +115,7 @@ struct BatchArgs {
     const long long* base;/* common step counter                                 */
     int* err;
     int tile_m, chunk_n, vec, grid;
+    int alt;              /* as StepArgs::alt, for the batch's total state     */
 };
 
 /* Arguments of the on-chip batched kernel (bte_resident.cu): clusters of C

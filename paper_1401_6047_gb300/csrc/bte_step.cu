@@ -307,7 +307,16 @@ __device__ __forceinline__ bool wait_neighbours(const unsigned* done, int tx, in
     }
 }
 
-template <typename T, int V, bool BATCH, bool PERSIST>
+/* One launch: step base + launch_i (one step), or A.nsteps steps of a
+ * persistent launch.  DOWN fixes the direction of the row walks (see the
+ * consumer loop): where the state is larger than L2 the host alternates it
+ * between consecutive one-step launches (launch_i even: upward, odd:
+ * downward), so that every step starts with the rows the step before wrote
+ * last -- the ones still in L2 (2049 x 8193 FP32: 537 MB of state against
+ * 129 MB of L2).  The two
+ * directions are separate instantiations, so each keeps its own register
+ * allocation.  A persistent launch walks upward every step. */
+template <typename T, int V, bool BATCH, bool PERSIST, bool DOWN>
 __global__ void __launch_bounds__(MaxBlock<T, V>::value)
     fused_step_kernel(StepArgs<T> A, BatchArgs<T> Bt, int launch_i, int parity) {
     constexpr int H = StepCfg<T>::H;
@@ -383,7 +392,7 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
     };
     auto pump = [&](long long kb, int cr) {
         while (p_item < items && p_issued < p_freed + RS) {
-            const int row = p_n0 - 2 + p_s;
+            const int row = DOWN ? p_n1 + 1 - p_s : p_n0 - 2 + p_s;
             const uint32_t mb = smem_u32(&bar[p_slot]);
             if (row < 0 || row > p_N) {
                 mbar_arrive(mb);
@@ -506,14 +515,23 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
             double part_n = 0.0, part_v = 0.0;
             int slot_m1 = 0, slot_m2 = 0; /* ring slots of the two previous stages */
 
-            /* stages 0 and 1 (old rows n0-2, n0-1) are consumed as row j+1 of the
-             * load-only iterations j = n0-3, n0-2 */
-            for (int j = n0 - 3; j <= n1; ++j) {
+            /* Row walk.  Upward (even steps): iteration j (j =
+             * n0 - 3 .. n1, stage si = j - n0 + 3) works on new whole row j
+             * after old row j + 1 arrived, and on new fractional row j - 1.
+             * Downward (odd steps), the mirror image: j = n1 + 2 .. n0 - 1
+             * (stage si = n1 + 2 - j), old row j - 1 arrives, fractional row
+             * j + 1 follows.  Each step then starts
+             * with the rows the previous step wrote last, which are still in
+             * L2.  The per-cell arithmetic is the same either way.  Stages 0
+             * and 1 are consumed by the load-only first two iterations. */
+            constexpr int dj = DOWN ? -1 : 1;
+            for (int j = DOWN ? n1 + 2 : n0 - 3; DOWN ? j >= n0 - 1 : j <= n1; j += dj) {
                 if (!mbar_wait(smem_u32(&bar[c_slot]), c_phase)) timed_out = true;
-                const T* ra = sF + (size_t)c_slot * 2 * LW; /* old fractional row j+1 */
+                const T* ra = sF + (size_t)c_slot * 2 * LW; /* the old fractional row that arrived */
+                const int jn = DOWN ? j - 1 : j + 1;         /* its index */
 
-                T fa_p1[V], fb_p1[V], dfa_p1[V], dfb_p1[V];
-                if (j + 1 >= 0 && j + 1 <= N && is_comp) {
+                T fa_p1[V], fb_p1[V], dfa_p1[V], dfb_p1[V]; /* row jn */
+                if (jn >= 0 && jn <= N && is_comp) {
                     T l, r;
                     ld_own<T, V>(ra + lc, fa_p1);
                     neighbours<T, V>(ra + lc, l, r);
@@ -526,7 +544,7 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
                     for (int e = 0; e < V; ++e) fa_p1[e] = fb_p1[e] = dfa_p1[e] = dfb_p1[e] = (T)0;
                 }
 
-                if (j >= n0 - 1) {
+                if (DOWN ? j <= n1 : j >= n0 - 1) { /* from the third stage on */
                     /* ---- new whole-grid row j ---- */
                     const bool wrow_ok = j >= 0 && j <= N;
                     T wa_n[V], wb_n[V];
@@ -541,8 +559,13 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
                             ld_own<T, V>(wa + lc, oa);
                             ld_own<T, V>(wa + LW + lc, ob);
                                 T an[V], bn[V];
-                            cn_row<T, V>(oa, ob, dfb_p1, dfb_m1, dfa_m1, dfa_p1, ccw, chi, hr, g,
-                                         nf, ws, we, K, an, bn);
+                            /* differences of old fractional rows j + 1 (next) and j - 1 (prev) */
+                            if constexpr (!DOWN)
+                                cn_row<T, V>(oa, ob, dfb_p1, dfb_m1, dfa_m1, dfa_p1, ccw, chi, hr, g,
+                                             nf, ws, we, K, an, bn);
+                            else
+                                cn_row<T, V>(oa, ob, dfb_m1, dfb_p1, dfa_p1, dfa_m1, ccw, chi, hr, g,
+                                             nf, ws, we, K, an, bn);
 #pragma unroll
                             for (int e = 0; e < V; ++e) {
                                 wa_n[e] = ok[e] ? an[e] : (T)0;
@@ -572,7 +595,11 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
                                 }
                             }
                         } else if (hlane) {
-                            const T* fd = sF + (size_t)slot_m2 * 2 * LW; /* old frac row j-1 */
+                            /* old fractional rows j - 1 and j + 1: the one that
+                             * arrived now and the one two stages back */
+                            const T* f2 = sF + (size_t)slot_m2 * 2 * LW;
+                            const T* fd = DOWN ? ra : f2; /* row j - 1 */
+                            const T* fu = DOWN ? f2 : ra; /* row j + 1 */
                             const bool dn = j - 1 >= 0, up = j + 1 <= N;
                             T oa2[2], ob2[2], dad[2], dbd[2], dau[2], dbu[2], an2[2], bn2[2];
 #pragma unroll
@@ -582,8 +609,8 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
                                 ob2[s2] = wa[LW + c2];
                                 dad[s2] = dn ? fd[c2 + 1] - fd[c2 - 1] : (T)0;
                                 dbd[s2] = dn ? fd[LW + c2 + 1] - fd[LW + c2 - 1] : (T)0;
-                                dau[s2] = up ? ra[c2 + 1] - ra[c2 - 1] : (T)0;
-                                dbu[s2] = up ? ra[LW + c2 + 1] - ra[LW + c2 - 1] : (T)0;
+                                dau[s2] = up ? fu[c2 + 1] - fu[c2 - 1] : (T)0;
+                                dbu[s2] = up ? fu[LW + c2 + 1] - fu[LW + c2 - 1] : (T)0;
                             }
                             cn_row<T, 2>(oa2, ob2, dbu, dbd, dad, dau, ccw, chi, hr, hg, nf, hbs,
                                          hbe, K, an2, bn2);
@@ -601,9 +628,11 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
                         break;
                     }
                     if (tid == NTr) {
-                        /* every stage up to old row j-1 has been read for the last time */
-                        const long long si = j - n0 + 3;
-                        const long long f = (j == n1) ? cbase + S : cbase + si - 1;
+                        /* every stage before stage si - 1 (si: this iteration's
+                         * stage) has been read for the last time; all of them
+                         * after the last iteration */
+                        const long long si = DOWN ? n1 + 2 - j : j - n0 + 3;
+                        const long long f = (si == S - 1) ? cbase + S : cbase + si - 1;
                         if (f > p_freed) p_freed = f;
                         fence_proxy_async_smem();
                         pump(kbase, cur);
@@ -621,14 +650,21 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
     #pragma unroll
                         for (int e = 0; e < V; ++e) dwa_0[e] = dwb_0[e] = (T)0;
                     }
-                    const int r = j - 1;
+                    /* ---- new fractional row r, one behind: it needs new whole
+                     * rows r - 1 and r + 1, the one just made (dw_0) and the
+                     * one two rows back (dw_m2) ---- */
+                    const int r = DOWN ? j + 1 : j - 1;
                     if (r >= n0 && r < n1 && is_comp && ok[0]) {
                         const T nf = (T)r;
                         const T chi = (r == 1) ? (T)2 : (T)1;
                         const T hr = O::mul(h, sR[r - n0 + 1]);
                         T fa_n[V], fb_n[V];
+                        if constexpr (!DOWN)
                             cn_row<T, V>(fa_m1, fb_m1, dwb_0, dwb_m2, dwa_m2, dwa_0, ccf, chi, hr, g,
-                                     nf, fs, fe, K, fa_n, fb_n);
+                                         nf, fs, fe, K, fa_n, fb_n);
+                        else
+                            cn_row<T, V>(fa_m1, fb_m1, dwb_m2, dwb_0, dwa_0, dwa_m2, ccf, chi, hr, g,
+                                         nf, fs, fe, K, fa_n, fb_n);
                         if (r == 0) {
 #pragma unroll
                             for (int e = 0; e < V; ++e) fb_n[e] = (T)0;
@@ -647,8 +683,8 @@ __global__ void __launch_bounds__(MaxBlock<T, V>::value)
                         }
                     }
 
-                    /* ---- observables of rows 0 and 1 ---- */
-                    if (n0 == 0 && j == 1) {
+                    /* ---- observables of rows 0 and 1, once both are made ---- */
+                    if (n0 == 0 && j == (DOWN ? 0 : 1)) {
                         const double sn = block_sum(part_n, red);
                         const double sv = block_sum(part_v, red);
                         if (tid == 0) {
@@ -785,23 +821,28 @@ int step_max_tile(int vec) {
     return 2 * (MaxBlock<double, 2>::value - 32);
 }
 
-template <typename T, bool BATCH, bool PERSIST>
+template <typename T, bool BATCH, bool PERSIST, bool DOWN>
 static const void* step_fn(int vec) {
     if constexpr (sizeof(T) == 4)
         return vec == 4
-                   ? reinterpret_cast<const void*>(&fused_step_kernel<float, 4, BATCH, PERSIST>)
-                   : reinterpret_cast<const void*>(&fused_step_kernel<float, 2, BATCH, PERSIST>);
+                   ? reinterpret_cast<const void*>(&fused_step_kernel<float, 4, BATCH, PERSIST, DOWN>)
+                   : reinterpret_cast<const void*>(&fused_step_kernel<float, 2, BATCH, PERSIST, DOWN>);
     else
-        return reinterpret_cast<const void*>(&fused_step_kernel<double, 2, BATCH, PERSIST>);
+        return reinterpret_cast<const void*>(&fused_step_kernel<double, 2, BATCH, PERSIST, DOWN>);
 }
 
 template <typename T, bool BATCH, bool PERSIST>
 static int configure(int tile_m, int chunk_n, int vec, int* blocks_per_sm) {
     const size_t bytes = step_smem_bytes<T>(tile_m, chunk_n, vec);
-    const void* fn = step_fn<T, BATCH, PERSIST>(vec);
+    const void* fn = step_fn<T, BATCH, PERSIST, false>(vec);
     cudaError_t e =
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return (int)e;
+    if (!PERSIST) {
+        e = cudaFuncSetAttribute(step_fn<T, BATCH, PERSIST, true>(vec),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return (int)e;
+    }
     int nb = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, step_block_threads<T>(tile_m, vec),
                                                       bytes);
@@ -845,13 +886,19 @@ static int launch(const StepArgs<T>& a, const BatchArgs<T>& b, int grid, int til
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaError_t e;
+    /* one-step launches of a state larger than L2 alternate the row-walk
+     * direction with launch_i */
+    const bool down = !PERSIST && (BATCH ? b.alt : a.alt) && (i & 1);
     if constexpr (sizeof(T) == 4) {
         if (vec == 4)
-            e = cudaLaunchKernelEx(&cfg, fused_step_kernel<float, 4, BATCH, PERSIST>, a, b, i, parity);
+            e = down ? cudaLaunchKernelEx(&cfg, fused_step_kernel<float, 4, BATCH, PERSIST, !PERSIST>, a, b, i, parity)
+                     : cudaLaunchKernelEx(&cfg, fused_step_kernel<float, 4, BATCH, PERSIST, false>, a, b, i, parity);
         else
-            e = cudaLaunchKernelEx(&cfg, fused_step_kernel<float, 2, BATCH, PERSIST>, a, b, i, parity);
+            e = down ? cudaLaunchKernelEx(&cfg, fused_step_kernel<float, 2, BATCH, PERSIST, !PERSIST>, a, b, i, parity)
+                     : cudaLaunchKernelEx(&cfg, fused_step_kernel<float, 2, BATCH, PERSIST, false>, a, b, i, parity);
     } else {
-        e = cudaLaunchKernelEx(&cfg, fused_step_kernel<double, 2, BATCH, PERSIST>, a, b, i, parity);
+        e = down ? cudaLaunchKernelEx(&cfg, fused_step_kernel<double, 2, BATCH, PERSIST, !PERSIST>, a, b, i, parity)
+                 : cudaLaunchKernelEx(&cfg, fused_step_kernel<double, 2, BATCH, PERSIST, false>, a, b, i, parity);
     }
     if (e != cudaSuccess) return (int)e;
     return ok_or(cudaGetLastError());

@@ -244,9 +244,8 @@ class Surrogate:
         status = np.zeros(n, dtype=np.int32)
         o = bte.bte_batch_opts()
         for k in ("tile_m", "chunk_n", "vec", "graph_steps", "max_batch", "max_batch_bytes",
-                  "resident", "resident_smem"):
+                  "resident", "resident_smem", "walk"):
             setattr(o, k, int(batch_opts.get(k, 0)))
-        o.reserved = 0
         o.stream = None
         rc = self._lib.bte_sur_hybrid(self._h, _p(x, ctypes.c_double), n, float(threshold),
                                       int(precision), ctypes.byref(o), _p(y, ctypes.c_double),

@@ -122,6 +122,48 @@ def test_random_state_parity(shape, prec, vec):
         assert _rel_arr(nr, n_ref) <= tol
 
 
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("prec,vec", [(W.FP64, 2), (W.FP32_MIXED, 2), (W.FP32_MIXED, 4)])
+def test_alternating_row_walk_parity(shape, prec, vec):
+    """The downward row walk (odd one-step launches with walk = 2; the
+    default for states larger than L2) against the oracle on a random state
+    of every launch shape, and equal bit for bit to walking upward every
+    step (walk = 1): the same per-cell arithmetic in another order.  Graphs
+    of 6 launches plus direct launches for the remaining 5 steps, so both
+    directions run in both launch forms."""
+    n_max, m_points, tile_m, chunk_n = shape
+    p = _rand_params(n_max, m_points, prec)
+    aw, bw, af, bf = W.random_state(p, seed=29 + n_max)
+    st = oracle.State(aw.copy(), bw.copy(), af.copy(), bf.copy())
+    v_ref, n_ref = oracle.advance(p, st, 0, 17)
+    got = {}
+    for walk in (1, 2):
+        with bte.Solver(p, tile_m=tile_m, chunk_n=chunk_n, graph_steps=6, vec=vec, walk=walk) as s:
+            s.set_state(0, aw, bw)
+            s.set_state(1, af, bf)
+            s.step(17)
+            got[walk] = (*s.get_state(0), *s.get_state(1), *s.trace(1, 17))
+            if walk == 2:
+                tol = RTOL64 if prec == W.FP64 else 2e-5
+                _cmp_state(s, st, tol, f"shape {shape}, alternating walk")
+                assert _rel_arr(got[2][4], v_ref) <= tol
+                assert _rel_arr(got[2][5], n_ref) <= tol
+    for x, y in zip(got[1], got[2]):
+        assert np.array_equal(x, y)
+
+
+def test_alternating_row_walk_batched_is_bitwise():
+    """The batched streamed tier with both walk orders: identical bits."""
+    pts = [_rand_params(20 + 3 * i, 161 + 40 * i, W.FP32_MIXED).replace(periods=0.3, avg_window=0.1)
+           for i in range(3)]
+    r1 = bte.batch_run(pts, resident=1, walk=1)
+    r2 = bte.batch_run(pts, resident=1, walk=2)
+    for a, b in zip(r1, r2):
+        assert a.status == bte.OK and b.status == bte.OK
+        assert a.absorption == b.absorption and a.v_dc_avg == b.v_dc_avg
+        assert a.norm_max_abs_err == b.norm_max_abs_err
+
+
 @pytest.mark.parametrize("prec", [W.FP64, W.FP32_MIXED])
 def test_c2_full_grid_short_run(prec):
     """401 x 4001 grid in the launch shape the benchmark times, 24 steps from
