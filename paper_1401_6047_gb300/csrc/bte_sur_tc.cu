@@ -67,7 +67,8 @@ constexpr size_t kOffW1s = kOffW1 + kHalfBytes;           /* W1 [256][5] */
 constexpr size_t kOffB = kOffW1s + (size_t)TH * kIn * 4;  /* b1, b2, b3 [256] each */
 constexpr size_t kOffW4 = kOffB + 3 * (size_t)TH * 4;     /* W4 [2][256], b4 [2] */
 constexpr size_t kOffRed = kOffW4 + (2 * (size_t)TH + 4) * 4; /* [4][128][2] partial outputs */
-constexpr size_t kOffBar = kOffRed + 4 * (size_t)TM * 2 * 4;
+constexpr size_t kOffX = kOffRed + 4 * (size_t)TM * 2 * 4;      /* [128][5] raw inputs */
+constexpr size_t kOffBar = kOffX + (size_t)TM * kIn * 4;
 /* barriers: wbar[2] (weight halves), cbar[4] (h chunks), mbar (MMA commits) */
 constexpr size_t kSmemTC = kOffBar + 128 + 1024; /* + alignment slack */
 
@@ -109,6 +110,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
     float* sB = reinterpret_cast<float*>(tsm + kOffB);
     float* sW4 = reinterpret_cast<float*>(tsm + kOffW4);
     float* red = reinterpret_cast<float*>(tsm + kOffRed);
+    float* sX = reinterpret_cast<float*>(tsm + kOffX);
     uint64_t* bars = reinterpret_cast<uint64_t*>(tsm + kOffBar);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tsm + kOffBar + 64);
     volatile int* abort = reinterpret_cast<volatile int*>(tsm + kOffBar + 72);
@@ -224,33 +226,64 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
         const int rl0 = (warp >> 3) * 64 + lane; /* layer 1: rows rl0, rl0 + 32 */
         const int erow = q * 32 + lane;          /* epilogue row (tensor-memory lane) */
         const uint32_t tl = (uint32_t)(q * 32) << 16;
+        /* the raw inputs of a tile's 128 rows go to shared memory by
+         * asynchronous 4-byte copies (zero-filled past nvalid), issued one
+         * tile ahead by warps 0 and 8 (rows rl0, rl0 + 32 of each lane) */
+        auto fetch_x = [&](int tile) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int rl = rl0 + 32 * j, row = tile * TM + rl;
+                const bool in = row < a.nvalid;
+                const float* src = a.x + (in ? (a.row0 + row) * kIn : 0);
+#pragma unroll
+                for (int i = 0; i < kIn; ++i)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                                     dev::smem_u32(sX + rl * kIn + i)),
+                                 "l"(src + i), "r"(in ? 4 : 0)
+                                 : "memory");
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        if (blockIdx.x < ntile && ug == 0) fetch_x(blockIdx.x);
         for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
             const bool run = !*abort;
             const int r0 = tile * TM;
             /* ---- layer 1 on the FP32 cores, chunk by chunk ---- */
+            if (ug == 0) asm volatile("cp.async.wait_all;" ::: "memory");
+            comp_sync(); /* every row's inputs have landed */
             float xh[2][kIn];
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                const int row = r0 + rl0 + 32 * j;
-                if (row < a.nvalid) {
-                    const long long s = a.row0 + row;
+                const int rl = rl0 + 32 * j;
+                const bool in = r0 + rl < a.nvalid;
 #pragma unroll
-                    for (int i = 0; i < kIn; ++i)
-                        xh[j][i] = 2.0f * (a.x[s * kIn + i] - a.sc.x_lo[i]) * a.sc.x_inv[i] - 1.0f;
-                } else {
-#pragma unroll
-                    for (int i = 0; i < kIn; ++i) xh[j][i] = 0.0f;
-                }
+                for (int i = 0; i < kIn; ++i)
+                    xh[j][i] = in ? 2.0f * (sX[rl * kIn + i] - a.sc.x_lo[i]) * a.sc.x_inv[i] - 1.0f : 0.0f;
             }
             for (int c = 0; c < kNChunk; ++c) {
                 if (run) {
                     const int u0 = c * kChunk + 8 * ug;
+                    /* W1 rows u0 .. u0 + 7 (40 values) and b1, as 16-byte loads */
                     float w[8][kIn], b[8];
+                    {
+                        float wf[8 * kIn];
+                        const float4* w4 = reinterpret_cast<const float4*>(sW1 + u0 * kIn);
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
+                        for (int q4 = 0; q4 < 2 * kIn; ++q4) {
+                            const float4 t = w4[q4];
+                            wf[4 * q4] = t.x;
+                            wf[4 * q4 + 1] = t.y;
+                            wf[4 * q4 + 2] = t.z;
+                            wf[4 * q4 + 3] = t.w;
+                        }
 #pragma unroll
-                        for (int i = 0; i < kIn; ++i) w[u][i] = sW1[(u0 + u) * kIn + i];
-                        b[u] = sB[u0 + u];
+                        for (int u = 0; u < 8; ++u)
+#pragma unroll
+                            for (int i = 0; i < kIn; ++i) w[u][i] = wf[u * kIn + i];
+                        const float4 b0 = reinterpret_cast<const float4*>(sB + u0)[0];
+                        const float4 b1v = reinterpret_cast<const float4*>(sB + u0)[1];
+                        b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
+                        b[4] = b1v.x; b[5] = b1v.y; b[6] = b1v.z; b[7] = b1v.w;
                     }
 #pragma unroll
                     for (int j = 0; j < 2; ++j) {
@@ -282,7 +315,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
                     const int col0 = c * kChunk + sc * 16;
                     float v[16];
                     tc_ld16(tmem + tl + (uint32_t)col0, v);
-                    const float* bias = sB + TH + col0;
+                    float bias[16];
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        const float4 t = reinterpret_cast<const float4*>(sB + TH + col0)[q4];
+                        bias[4 * q4] = t.x;
+                        bias[4 * q4 + 1] = t.y;
+                        bias[4 * q4 + 2] = t.z;
+                        bias[4 * q4 + 3] = t.w;
+                    }
 #pragma unroll
                     for (int h8 = 0; h8 < 16; h8 += 8) {
                         __nv_bfloat162 pk[4];
@@ -302,17 +343,27 @@ __global__ void __launch_bounds__(kThreadsTC, 1) infer_tc_kernel(InferArgs a) {
             /* ---- layer 3 epilogue fused with the output layer (N = 2) ---- */
             const bool ok3 = ok2 && wait_or_abort(bM, 1u, abort);
             tc_fence_after();
+            /* the next tile's inputs (layer 1 of this tile has read sX) */
+            if (ug == 0 && tile + (int)gridDim.x < ntile) fetch_x(tile + gridDim.x);
             float y0 = 0.0f, y1 = 0.0f;
             if (ok3) {
-                for (int cb = 0; cb < 2; ++cb) {
-                    const int col0 = sc * 64 + cb * 32;
-                    float v[32];
-                    tc_ld32(tmem + tl + (uint32_t)(TH + col0), v);
-                    const float* bias = sB + 2 * TH + col0;
-                    const float* w40 = sW4 + col0;
-                    const float* w41 = sW4 + TH + col0;
+#pragma unroll 1
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    const int col0 = sc * 64 + 16 * q4;
+                    float v[16];
+                    tc_ld16(tmem + tl + (uint32_t)(TH + col0), v);
+                    float bias[16], w40[16], w41[16];
 #pragma unroll
-                    for (int e = 0; e < 32; e += 2) {
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        const float4 tb = reinterpret_cast<const float4*>(sB + 2 * TH + col0)[k4];
+                        const float4 t0 = reinterpret_cast<const float4*>(sW4 + col0)[k4];
+                        const float4 t1 = reinterpret_cast<const float4*>(sW4 + TH + col0)[k4];
+                        bias[4 * k4] = tb.x; bias[4 * k4 + 1] = tb.y; bias[4 * k4 + 2] = tb.z; bias[4 * k4 + 3] = tb.w;
+                        w40[4 * k4] = t0.x; w40[4 * k4 + 1] = t0.y; w40[4 * k4 + 2] = t0.z; w40[4 * k4 + 3] = t0.w;
+                        w41[4 * k4] = t1.x; w41[4 * k4 + 1] = t1.y; w41[4 * k4 + 2] = t1.z; w41[4 * k4 + 3] = t1.w;
+                    }
+#pragma unroll
+                    for (int e = 0; e < 16; e += 2) {
                         /* h3 rounded to BF16 as the operand of a tensor-core layer would be */
                         const float2 hf = __bfloat1622float2(
                             __floats2bfloat162_rn(silu_tc(v[e] + bias[e]), silu_tc(v[e + 1] + bias[e + 1])));

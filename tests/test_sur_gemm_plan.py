@@ -9,7 +9,7 @@ global read stays inside its operand, every shared-memory write inside its
 decoded from the descriptors equals A B^T for all three operand layouts the
 training pass uses.  Mirrors the arithmetic of gemm_tc_kernel and
 load_stage in csrc/bte_sur_kernels.cu; the last test does the same for the
-inference kernel's operand and weight-chunk layouts (csrc/bte_sur_tc.cu)."""
+inference kernel's operand and weight layouts (csrc/bte_sur_tc.cu)."""
 import numpy as np
 import pytest
 
@@ -103,50 +103,42 @@ def test_stage_fill_and_descriptors_give_a_times_b_transposed(amn, bmn):
     assert np.array_equal(C, A @ B.T)
 
 
-def test_inference_weight_chunks_and_operand_decode_through_descriptors():
-    """Inference kernel (csrc/bte_sur_tc.cu): W2/W3 stored per 64-input
-    K-chunk ([256 outputs][64 inputs], 8-row groups 1024 bytes apart) and
-    h stored [128 rows][256] (8-row groups 4096 bytes apart).  Decoding the
-    MMAs of chunk c, weight half hh, K-step k4 through their descriptors
-    (start = slot + hh * 16 KB + k4 * 256 for the weights, h + (4 c + k4) *
-    256 for the operand; K-adjacent core matrices 128 bytes apart) gives
-    back W[128 hh + n][64 c + 16 k4 + kk] and h[r][64 c + 16 k4 + kk]."""
-    def wcanon(n, k):
-        return ((n >> 3) * 8 + (k >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2
-
+def test_inference_weights_and_operand_decode_through_descriptors():
+    """Inference kernel (csrc/bte_sur_tc.cu): W2/W3 stored as two halves of
+    128 output rows ([128][256] each) and h stored [128 rows][256], both
+    canonical with 8-row groups 4096 bytes apart.  Decoding the MMAs of
+    K-step ks (start = base + ks * 256; K-adjacent core matrices 128 bytes
+    apart) for weight half hh gives back h[r][16 ks + kk] and
+    W[128 hh + n][16 ks + kk], so the 2 x 16 MMAs of a layer compute h W^T."""
     def canon(r, k):
         return ((r >> 3) * 32 + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2
 
     rng = np.random.default_rng(3)
     W = rng.integers(-1000, 1000, size=(256, 256))
     h = rng.integers(-1000, 1000, size=(128, 256))
-    chunks = []
-    for c in range(4):
-        img = np.full(256 * 64, -10**9, dtype=np.int64)
-        for n in range(256):
-            for k in range(64):
-                off = wcanon(n, k)
-                assert 0 <= off < 32768 and off % 2 == 0
-                img[off // 2] = W[n, 64 * c + k]
-        assert np.all(img >= -1000), "every byte of the chunk written"
-        chunks.append(img)
+    halves = []
+    for hh in range(2):
+        img = np.full(128 * 256, -10**9, dtype=np.int64)
+        for n in range(128):
+            for k in range(256):
+                off = canon(n, k)
+                assert 0 <= off < 65536 and off % 2 == 0
+                img[off // 2] = W[128 * hh + n, k]
+        assert np.all(img >= -1000), "every byte of the half written"
+        halves.append(img)
     himg = np.full(128 * 256, -10**9, dtype=np.int64)
     for r in range(128):
         for k in range(256):
             himg[canon(r, k) // 2] = h[r, k]
     assert np.all(himg >= -1000), "every byte of h written"
+
+    def read(img, ks, r, kk):
+        return img[(ks * 256 + (kk >> 3) * 128 + (r >> 3) * 4096 + (r & 7) * 16 + (kk & 7) * 2) // 2]
+
     acc = np.zeros((128, 256), dtype=np.int64)
-    for c in range(4):
-        for hh in range(2):
-            for k4 in range(4):
-                ks = 4 * c + k4
-                a = np.zeros((128, 16), dtype=np.int64)
-                b = np.zeros((128, 16), dtype=np.int64)
-                for r in range(128):
-                    for kk in range(16):
-                        a[r, kk] = himg[(ks * 256 + (kk >> 3) * 128 + (r >> 3) * 4096 + (r & 7) * 16
-                                         + (kk & 7) * 2) // 2]
-                        b[r, kk] = chunks[c][(hh * 16384 + k4 * 256 + (kk >> 3) * 128 + (r >> 3) * 1024
-                                              + (r & 7) * 16 + (kk & 7) * 2) // 2]
-                acc[:, 128 * hh:128 * hh + 128] += a @ b.T
+    for hh in range(2):
+        for ks in range(16):
+            a = np.array([[read(himg, ks, r, kk) for kk in range(16)] for r in range(128)])
+            b = np.array([[read(halves[hh], ks, n, kk) for kk in range(16)] for n in range(128)])
+            acc[:, 128 * hh:128 * hh + 128] += a @ b.T
     assert np.array_equal(acc, h @ W.T)
