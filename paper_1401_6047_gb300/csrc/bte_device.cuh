@@ -51,19 +51,37 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+/* The same test with a suspend-time hint: the thread may sleep in the
+ * barrier unit for up to `ns` nanoseconds (it wakes when the phase
+ * completes) instead of returning at once, so a waiting warp takes few
+ * issue slots from the warps doing work. */
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
 /* Default limit of a bounded wait: 2 s of %globaltimer. */
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 /* Bounded wait on an mbarrier phase: false once limit_ns of %globaltimer
- * have passed without the phase completing. */
+ * have passed without the phase completing.  Retries sleep in the barrier
+ * unit (up to 10 us each, woken by the phase; never past the limit). */
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
                                           uint64_t limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer();
-    while (!mbar_try_wait(bar, parity)) {
-        if (global_timer() - t0 > limit_ns) return false;
+    for (;;) {
+        const uint64_t el = global_timer() - t0;
+        if (el > limit_ns) return false;
+        const uint64_t left = limit_ns - el;
+        if (mbar_try_wait_sleep(bar, parity, left < 10000u ? (uint32_t)left + 1u : 10000u)) return true;
     }
-    return true;
 }
 
 /* TMA bulk copy global -> shared, completion counted on an mbarrier.  Both

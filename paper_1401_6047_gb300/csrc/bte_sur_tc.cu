@@ -82,11 +82,12 @@ __host__ __device__ __forceinline__ uint32_t canon(int r, int k) {
 }
 
 /* Bounded mbarrier wait that also gives up at once when another thread of
- * the CTA has raised the abort flag; a wait that runs out raises it. */
+ * the CTA has raised the abort flag; a wait that runs out raises it.  Each
+ * retry may sleep up to 10 us in the barrier unit (woken by the phase). */
 __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort) {
     if (dev::mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = dev::global_timer();
-    while (!dev::mbar_try_wait(bar, parity)) {
+    while (!dev::mbar_try_wait_sleep(bar, parity, 10000u)) {
         if (*abort) return false;
         if (dev::global_timer() - t0 > dev::kWaitLimitNs) {
             *abort = 1;
