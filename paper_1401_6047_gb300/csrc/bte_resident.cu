@@ -90,13 +90,14 @@ __device__ __forceinline__ void diff_sh(const T* p, bool l_adj, bool r_adj, T (&
 }
 
 /* central differences of a group with the outer neighbours loaded (any
- * address space: used where a row may be a neighbour CTA's) */
+ * address space: used where a row may be a neighbour CTA's; the group's own
+ * values as one 16-byte load, so a neighbour's row costs three distributed
+ * shared-memory loads instead of six) */
 template <typename T>
 __device__ __forceinline__ void diff_ld(const T* p, T (&d)[RV<T>::V]) {
     constexpr int V = RV<T>::V;
     T own[V];
-#pragma unroll
-    for (int e = 0; e < V; ++e) own[e] = p[e];
+    ld_vec<T>(p, own);
     const T left = p[-1], right = p[V];
     d[0] = own[1] - left;
 #pragma unroll
@@ -173,6 +174,30 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+/* Sums of FP32 values carried as unevaluated pairs hi + lo of FP32 numbers
+ * (Knuth's error-free TwoSum, so the pair keeps about 48 bits): the per-step
+ * row sums of FP32 states need FP64-grade accuracy, and FP32 operations run
+ * at many times the rate of FP64 ones on this GPU. */
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return F2{s, e};
+}
+__device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
+    const F2 s = two_sum(x.hi, y.hi);
+    return two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ double warp_sum_f2(F2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = f2_add(v, F2{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)});
+    return (double)v.hi + (double)v.lo;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
     constexpr int V = RV<T>::V;
@@ -243,6 +268,7 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
         /* window accumulators in shared memory (thread 0 of rank 0 only
          * touches them; keeping them out of every thread's registers) */
         double* acc = red + 64 + 2; /* [6], after the warp partials and s_next */
+        double* rot = acc + 6;      /* [4]: window cos, sin and the per-step rotation */
         if (tid == 0)
             for (int q = 0; q < 6; ++q) acc[q] = 0.0;
         /* neighbours' shared memory (the four arrays of a CTA are contiguous,
@@ -360,9 +386,21 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
          * half-step runs (that half-step leaves the whole grid unchanged);
          * thread 0 folds the warp partials into the window sums after the
          * step's last block barrier. */
+        /* drive phase (k0 + k) mod P of step k, kept as a counter */
+        int kk = PP > 0 ? (int)(I.k0 % PP) : 0;
+        /* thread 0 of rank 0: cos of the window phase 2 pi ((k + 1) mod P) / P,
+         * advanced by one rotation per step and reset to its exact value at
+         * the start of every period (rounding grows over at most P steps) */
+        int kc = PP > 0 ? 1 % PP : 0;
+        if (rank == 0 && tid == 0) {
+            const double two_pi = 6.283185307179586476925286766559;
+            rot[0] = PP > 0 ? cos(two_pi * (double)kc / (double)PP) : 1.0;
+            rot[1] = PP > 0 ? sin(two_pi * (double)kc / (double)PP) : 0.0;
+            rot[2] = PP > 0 ? cos(two_pi / (double)PP) : 1.0;
+            rot[3] = PP > 0 ? sin(two_pi / (double)PP) : 0.0;
+        }
         cluster_arrive(); /* initial state loaded */
         for (long long k = 0; k < K; ++k) {
-            const int kk = PP > 0 ? (int)((I.k0 + k) % PP) : 0;
             const Half<T> Dw = half_drive<T>(I.e_whole, I.dstride, kk);
             const Half<T> Df = half_drive<T>(I.e_frac, I.dstride, kk);
             /* ---- whole grid: z_w^{k+1} = T(z_w^k; S(z_f^{k+1/2})) ---- */
@@ -373,20 +411,41 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
             cluster_arrive();
             if (rank == 0) {
                 /* local rows 0 and 1 are shared rows 1 and 2; without a row 1
-                 * (N = 0) shared row 2 is a zero halo row */
-                double pn = 0.0, pv = 0.0;
-                for (int g = tid; g < ncg; g += nthr) {
-                    T va[V], vb[V];
-                    ld_vec<T>(sAw + P + LG + g * V, va);
-                    ld_vec<T>(sBw + 2 * P + LG + g * V, vb);
+                 * (N = 0) shared row 2 is a zero halo row.  FP64 states add in
+                 * FP64; FP32 states in hi + lo pairs of FP32 (FP64-grade) */
+                double pn, pv;
+                if constexpr (sizeof(T) == 8) {
+                    pn = 0.0;
+                    pv = 0.0;
+                    for (int g = tid; g < ncg; g += nthr) {
+                        T va[V], vb[V];
+                        ld_vec<T>(sAw + P + LG + g * V, va);
+                        ld_vec<T>(sBw + 2 * P + LG + g * V, vb);
 #pragma unroll
-                    for (int e = 0; e < V; ++e) {
-                        pn += (double)va[e];
-                        pv += (double)vb[e];
+                        for (int e = 0; e < V; ++e) {
+                            pn += (double)va[e];
+                            pv += (double)vb[e];
+                        }
                     }
+                    pn = warp_sum(pn);
+                    pv = warp_sum(pv);
+                } else {
+                    F2 fn{0.0f, 0.0f}, fv{0.0f, 0.0f};
+                    for (int g = tid; g < ncg; g += nthr) {
+                        T va[V], vb[V];
+                        ld_vec<T>(sAw + P + LG + g * V, va);
+                        ld_vec<T>(sBw + 2 * P + LG + g * V, vb);
+#pragma unroll
+                        for (int e = 0; e < V; ++e) {
+                            const F2 tn = two_sum(fn.hi, (float)va[e]);
+                            fn = F2{tn.hi, __fadd_rn(fn.lo, tn.lo)};
+                            const F2 tv = two_sum(fv.hi, (float)vb[e]);
+                            fv = F2{tv.hi, __fadd_rn(fv.lo, tv.lo)};
+                        }
+                    }
+                    pn = warp_sum_f2(fn);
+                    pv = warp_sum_f2(fv);
                 }
-                pn = warp_sum(pn);
-                pv = warp_sum(pv);
                 if (lane == 0) {
                     red[warp] = pn;
                     red[32 + warp] = pv;
@@ -407,11 +466,20 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                 const double vv = I.vscale * sv, nn = I.nscale * sn;
                 const long long k1 = k + 1;
                 if (k1 > K - Kw) {
-                    const double ang = PP > 0 ? 6.283185307179586476925286766559 *
-                                                    (double)(k1 % PP) / (double)PP
-                                              : I.omega * (double)k1 * I.dt_eff;
-                    acc[0] += vv * cos(ang);
+                    /* omega = 0 (P = 0): the angle omega t is 0 */
+                    acc[0] += vv * rot[0];
                     acc[1] += vv;
+                }
+                if (PP > 0) {
+                    if (++kc == PP) {
+                        kc = 0;
+                        rot[0] = 1.0;
+                        rot[1] = 0.0;
+                    } else {
+                        const double c = rot[0], sn = rot[1];
+                        rot[0] = c * rot[2] - sn * rot[3];
+                        rot[1] = sn * rot[2] + c * rot[3];
+                    }
                 }
                 acc[2] = fmax(acc[2], fabs(nn - 1.0));
                 if (!isfinite(vv) || !isfinite(nn)) acc[3] = 1.0;
@@ -422,6 +490,7 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                     I.trace_n[I.k0 + k1] = nn;
                 }
             }
+            if (PP > 0 && ++kk == PP) kk = 0; /* P = 0 (omega = 0): row 0 every step */
         }
         cluster_wait(); /* pairs the last arrive */
 
@@ -455,7 +524,7 @@ size_t resident_smem_bytes(int N, int M, int C, size_t* arrays_bytes) {
     size_t b = (4 * arr + 2 * P + rows_per + 2) * sizeof(T);
     b = (b + 15) / 16 * 16;
     if (arrays_bytes) *arrays_bytes = b;
-    return b + 64 * sizeof(double) + 16 + 6 * sizeof(double);
+    return b + 64 * sizeof(double) + 16 + 10 * sizeof(double);
 }
 
 template <typename T>
