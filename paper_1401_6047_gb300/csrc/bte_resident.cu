@@ -8,8 +8,11 @@
  * row above and below.  A time step is the two half-steps of the leap-frog
  * scheme (Eqs. leap_frog_1, leap_frog_2), each applied in place -- the whole
  * grid's update reads only the fractional grid and each cell's own value,
- * and vice versa -- with a cluster barrier after each half-step and the
- * halo rows then read from the neighbouring CTAs' shared memory.  Per-cell
+ * and vice versa -- with a cluster barrier after each half-step.  A CTA
+ * writes its first and last rows also into the halo rows of the
+ * neighbouring CTAs (distributed shared memory) as it makes them, so that
+ * after the barrier every row a CTA reads is in its own shared memory.
+ * Per-cell
  * operations are those of the streaming kernel, in the same order (the
  * compiler may still contract multiply-adds differently); the per-step sums
  * of rows 0 and 1 (Eqs. v_dr_generic, norm_in_phi) are added in another
@@ -89,10 +92,8 @@ __device__ __forceinline__ void diff_sh(const T* p, bool l_adj, bool r_adj, T (&
     d[V - 1] = right - own[V - 2];
 }
 
-/* central differences of a group with the outer neighbours loaded (any
- * address space: used where a row may be a neighbour CTA's; the group's own
- * values as one 16-byte load, so a neighbour's row costs three distributed
- * shared-memory loads instead of six) */
+/* central differences of a group with the outer neighbours loaded (the
+ * group's own values as one 16-byte load) */
 template <typename T>
 __device__ __forceinline__ void diff_ld(const T* p, T (&d)[RV<T>::V]) {
     constexpr int V = RV<T>::V;
@@ -136,7 +137,8 @@ __device__ __forceinline__ void cell_group(T* oA, T* oB, const T (&da_u)[RV<T>::
                                            const T (&db_d)[RV<T>::V], int n, int m0, int M, T hr,
                                            const T (&gc)[RV<T>::V], const T (&t0)[RV<T>::V],
                                            const T (&t1)[RV<T>::V], const CnK<T>& K, T cc,
-                                           bool on) {
+                                           bool on, T* remU = nullptr, T* remD = nullptr,
+                                           size_t rem_db = 0) {
     constexpr int V = RV<T>::V;
     T oa[V], ob[V], an[V], bn[V], na[V], nb[V];
     ld_vec<T>(oA, oa);
@@ -152,6 +154,17 @@ __device__ __forceinline__ void cell_group(T* oA, T* oB, const T (&da_u)[RV<T>::
     if (!on) return;
     st_vec<T>(oA, na);
     st_vec<T>(oB, nb);
+    /* a boundary row also goes to the halo rows of the neighbouring CTAs
+     * that read it in the next half-step (distributed shared memory;
+     * rem_db: element offset of the b array from the a array) */
+    if (remU) {
+        st_vec<T>(remU, na);
+        st_vec<T>(remU + rem_db, nb);
+    }
+    if (remD) {
+        st_vec<T>(remD, na);
+        st_vec<T>(remD + rem_db, nb);
+    }
 }
 
 /* split cluster barrier (all threads of every CTA of the cluster) */
@@ -271,14 +284,17 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
         double* rot = acc + 6;      /* [4]: window cos, sin and the per-step rotation */
         if (tid == 0)
             for (int q = 0; q < 6; ++q) acc[q] = 0.0;
-        /* neighbours' shared memory (the four arrays of a CTA are contiguous,
-         * arr elements apart): row r0-1 is the last row of rank-1 (its local
-         * row rows_per-1, shared row rows_per), row r1 the first row of
-         * rank+1 (shared row 1).  Rows outside 0..N read this CTA's own zero
-         * halo rows (shared rows 0 and R+1, never written). */
+        /* halo rows: shared row 0 holds row r0-1 (the last row of rank-1),
+         * shared row R+1 row r1 (the first row of rank+1), both as loaded
+         * and then as the neighbours push them each half-step (the four
+         * arrays of a CTA are contiguous, arr elements apart).  Rows outside
+         * 0..N are halo rows that stay zero (no neighbour writes them). */
         const bool have_up = r0 >= 1 && R > 0, have_dn = r1 <= N && R > 0;
-        const T* nbr_up = have_up ? cl.map_shared_rank(sAw, rank - 1) + (size_t)rows_per * P : sAw;
-        const T* nbr_dn = have_dn ? cl.map_shared_rank(sAw, rank + 1) + (size_t)P : sAw;
+        /* a CTA's first own row is the halo row below the last own row of
+         * rank-1 (its shared row rows_per + 1), its last own row the halo
+         * row above rank+1's first (its shared row 0) */
+        T* halo_up = have_up ? cl.map_shared_rank(sAw, rank - 1) + (size_t)(rows_per + 1) * P : nullptr;
+        T* halo_dn = have_dn ? cl.map_shared_rank(sAw, rank + 1) : nullptr;
 
         /* interior rows 1..R-2 read only this CTA's rows: thread -> (column
          * group gl, row block rp), fixed for the point.  A block of nrow
@@ -356,10 +372,10 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                 const int il = b == 0 ? 0 : R - 1;
                 const int m0 = g * V;
                 const size_t c = (size_t)(il + 1) * P + LG + m0;
-                /* rows il-1 and il+1 of the other grid: local, or a neighbour's */
-                const T* up = (il == 0 && have_up) ? nbr_up + x * arr + LG + m0 : sAw + x * arr + c - P;
-                const T* dn = (il == R - 1 && have_dn) ? nbr_dn + x * arr + LG + m0
-                                                       : sAw + x * arr + c + P;
+                /* rows il-1 and il+1 of the other grid, halo rows included:
+                 * all in this CTA's shared memory */
+                const T* up = sAw + x * arr + c - P;
+                const T* dn = sAw + x * arr + c + P;
                 T da_u[V], da_d[V], db_u[V], db_d[V];
                 diff_ld<T>(up, da_u);
                 diff_ld<T>(dn, da_d);
@@ -373,9 +389,11 @@ __global__ void __launch_bounds__(512, 1) resident_kernel(ResArgs<T> A) {
                     t0[e] = rot_factor<T>(D.E0, D.B0, ph, hh);
                     t1[e] = rot_factor<T>(D.E1, D.B1, ph, hh);
                 }
+                T* remU = (il == 0 && halo_up) ? halo_up + o * arr + LG + m0 : nullptr;
+                T* remD = (il == R - 1 && halo_dn) ? halo_dn + o * arr + LG + m0 : nullptr;
                 cell_group<T>(sAw + o * arr + c, sAw + (o + 1) * arr + c, da_u, da_d, db_u, db_d,
                               r0 + il, m0, M, Rn<T>::mul(h, sR[il + 1]), gc, t0, t1, cn, D.cc,
-                              true);
+                              true, remU, remD, arr);
             }
         };
 

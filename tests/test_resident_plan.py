@@ -1,15 +1,16 @@
 """Host-side check of the on-chip batched kernel's work partition and
 shared-memory indices (csrc/bte_resident.cu), restated here in Python: for
 every rank of a cluster and every thread of a 512-thread CTA, the interior
-row chains, the boundary-row units, the row-0/1 sums and the initial load.
+row chains, the boundary-row units and the edge rows they push into the
+neighbours' halo rows, the row-0/1 sums and the initial load.
 
 Checked for each shape: every shared-memory access lies inside its array
 (rows 0 .. rows_per+1, columns 0 .. P-1), reads and writes alike, including
 the clamped iterations that store nothing; every row of the CTA is written
 exactly once per half-step (interior chains plus boundary units); rows
 outside 0..N are only ever read from the zero halo rows that nothing
-writes; a neighbour's row read through distributed shared memory is that
-neighbour's first or last own row.  No GPU is needed: the kernel's index
+writes; a row pushed into a neighbour's halo row (distributed shared
+memory) is the row that halo row stands for.  No GPU is needed: the kernel's index
 arithmetic is evaluated for all threads on the CPU."""
 import itertools
 
@@ -86,27 +87,27 @@ def _check_shape(N1, M1, C, V):
                         assert 0 <= il + 1 <= rows_per + 1       # sR[il + 1]
                         if on:
                             write(il + 1, g)
-        # boundary rows 0 and R-1
+        # boundary rows 0 and R-1: every read in this CTA's shared memory
+        # (the halo rows hold the neighbours' edge rows, pushed to them)
         nbnd = 2 if R >= 2 else R
         for tid in range(NTHR):
             for u in range(tid, nbnd * ncg, NTHR):
                 b, g = divmod(u, ncg)
                 il = 0 if b == 0 else R - 1
                 m0 = g * V
-                if il == 0 and have_up:
-                    _, _, Rn = rank_rows(rank - 1)
-                    assert Rn == rows_per                       # its last own row is shared row rows_per
-                    read(rows_per, LG + m0 - 1, LG + m0 + V, own=False)
-                else:
-                    read(il, LG + m0 - 1, LG + m0 + V)
-                if il == R - 1 and have_dn:
-                    _, _, Rn = rank_rows(rank + 1)
-                    assert Rn >= 1                              # its first own row is shared row 1
-                    read(1, LG + m0 - 1, LG + m0 + V, own=False)
-                else:
-                    read(il + 2, LG + m0 - 1, LG + m0 + V)
+                read(il, LG + m0 - 1, LG + m0 + V)
+                read(il + 2, LG + m0 - 1, LG + m0 + V)
                 read(il + 1, LG + m0, LG + m0 + V - 1)
                 write(il + 1, g)
+                if il == 0 and have_up:
+                    # pushed into rank-1's halo row below its last own row
+                    _, r1n, Rn = rank_rows(rank - 1)
+                    assert Rn == rows_per and r1n == r0
+                    assert rows_per + 1 > Rn                    # a halo row, not one of its own rows
+                if il == R - 1 and have_dn:
+                    # pushed into rank+1's halo row 0, which stands for row r1 - 1
+                    r0n, _, Rn = rank_rows(rank + 1)
+                    assert Rn >= 1 and r0n - 1 == r0 + R - 1      # shared row 0 is not one of its own rows
         # every own row written exactly once per half-step
         assert set(written) == {(s, g) for s in range(1, R + 1) for g in range(ncg)}, (N1, M1, C, rank)
         assert all(c == 1 for c in written.values()), (N1, M1, C, rank)
