@@ -289,15 +289,19 @@ def run_ours(args):
         # persistent mode also where L2 holds the state (401x4001: 17.4 vs
         # 20.9 us per step; the Table 1 run: 14.1 vs 16.1)
         mode = "streamed"
-    resident = {"streamed": 0, "on-chip": 1, "persistent": 2}[mode]
-    on_chip = resident == 1
+    resident = {"streamed": 0, "on-chip": 1, "persistent": 2, "on-chip-clusters": 3}[mode]
+    on_chip = resident in (1, 3)
     solver = bte.Solver(p, stream=stream.cuda_stream, tile_m=args.tile_m, chunk_n=args.chunk_n,
                         graph_steps=args.graph_steps, vec=args.vec, resident=resident)
     graph_len = min(args.graph_steps or 1024, K)
-    if on_chip:
+    if resident == 1:
         # init, start-up half step, step-0 observables; one on-chip launch and
         # the step-counter update; finalize
         launches_per_solve = 3 + 2 + 1
+    elif resident == 3:
+        # set-up as above; per 8192 steps the on-chip launch over clusters,
+        # the fold of its per-cluster sums and a counter update; finalize
+        launches_per_solve = 3 + 3 * (-(-K // 8192)) + 1
     elif mode == "persistent":
         # set-up as above; per 8192 steps one persistent launch and a counter
         # update; finalize
@@ -429,6 +433,10 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}",
                        "mode": {"on-chip": "on chip: the grid in one thread-block cluster's "
                                            "shared memory, one persistent launch per solve",
+                                "on-chip-clusters": "on chip over several clusters: column blocks "
+                                                    "in the shared memory of one cluster each, edge "
+                                                    "columns exchanged through global memory, one "
+                                                    "launch per 8192 steps",
                                 "persistent": "persistent: one cooperative launch per 8192 steps, "
                                               "grid barrier between steps, state in L2",
                                 "streamed": "streamed: one fused step kernel launch per step, "
@@ -441,6 +449,7 @@ def run_ours(args):
                          "peak_source": peak_source,
                          "hbm_frac": achieved / hbm_peak,
                          "kernel": {"on-chip": "resident_kernel (per step)",
+                                    "on-chip-clusters": "wide_kernel (per step)",
                                     "persistent": "fused_step_kernel, persistent (per step)",
                                     "streamed": "fused_step_kernel"}[mode],
                          "alg_bytes_per_launch": alg_bytes,
@@ -1096,7 +1105,8 @@ def main():
     ap.add_argument("--resident-smem", dest="resident_smem", type=int, default=0,
                     help="c4: shared memory per CTA for on-chip points (bytes)")
     ap.add_argument("--max-batch-bytes", dest="max_batch_bytes", type=int, default=0)
-    ap.add_argument("--mode", default="auto", choices=["auto", "streamed", "persistent", "on-chip"],
+    ap.add_argument("--mode", default="auto",
+                    choices=["auto", "streamed", "persistent", "on-chip", "on-chip-clusters"],
                     help="single-instance mode (auto: streamed, one launch per step)")
     ap.add_argument("--on-chip", dest="on_chip", action="store_true",
                     help="single-instance configs: keep the grid in one cluster's shared memory")

@@ -142,6 +142,24 @@ typedef struct {
                             On a GB300 it is slower than mode 0 on the
                             grids measured (401 x 4001 FP32: 20.9 against
                             17.4 us per step).
+                            3: on chip over several clusters -- the grid
+                            cut into G column blocks (one cluster of C CTAs
+                            each, C as for 1) whose CTAs keep their part of
+                            the four arrays in shared memory; each
+                            bte_step/bte_run call is one launch per 8192
+                            steps of G x C CTAs, all resident at once (a
+                            cooperative launch), that exchange their edge
+                            columns through global memory behind
+                            release/acquire completion counters, polled
+                            with a %globaltimer bound (BTE_ETIMEOUT when a
+                            wait gives up).  Per-cell arithmetic as in mode
+                            0; the per-step sums of rows 0 and 1 are added
+                            per cluster, then over clusters in order.
+                            One thread per cell: BTE_EINVAL when a CTA's
+                            block has more than 480 cells or does not fit
+                            232,448 bytes, or the G clusters do not fit the
+                            GPU at once (small grids: 31 x 201 FP64 runs
+                            7.0 instead of 16.1 us per step on a GB300).
                             0: one fused step kernel launch per step.      */
     int32_t walk;        /* order in which one-step launches walk the
                             harmonic rows of a work item: 0 automatic
@@ -151,6 +169,11 @@ typedef struct {
                             upward otherwise), 1 upward every step, 2
                             alternate every step.  The results are the same
                             bits in every order.                           */
+    int32_t wide_cols;   /* resident = 3: phi_y columns per cluster, 1..4096,
+                            at most 32 clusters (0: automatic -- about 32
+                            columns per cluster in FP64, 64 in FP32, at
+                            most 128 CTAs in all and no more clusters than
+                            fit the GPU at once)                           */
 } bte_tuning;
 
 typedef struct bte_handle bte_handle;

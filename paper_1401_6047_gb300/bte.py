@@ -52,7 +52,8 @@ class bte_obs(ctypes.Structure):
 class bte_tuning(ctypes.Structure):
     _fields_ = [("tile_m", ctypes.c_int32), ("chunk_n", ctypes.c_int32),
                 ("graph_steps", ctypes.c_int32), ("vec", ctypes.c_int32),
-                ("resident", ctypes.c_int32), ("walk", ctypes.c_int32)]
+                ("resident", ctypes.c_int32), ("walk", ctypes.c_int32),
+                ("wide_cols", ctypes.c_int32)]
 
 
 class bte_batch_opts(ctypes.Structure):
@@ -147,10 +148,10 @@ def to_params(p) -> bte_params:
     return s
 
 
-def _tuning(tile_m=0, chunk_n=0, graph_steps=0, vec=0, resident=0, walk=0):
+def _tuning(tile_m=0, chunk_n=0, graph_steps=0, vec=0, resident=0, walk=0, wide_cols=0):
     t = bte_tuning()
     t.tile_m, t.chunk_n, t.graph_steps, t.vec = int(tile_m), int(chunk_n), int(graph_steps), int(vec)
-    t.resident, t.walk = int(resident), int(walk)
+    t.resident, t.walk, t.wide_cols = int(resident), int(walk), int(wide_cols)
     return t
 
 
@@ -173,9 +174,9 @@ def time_grid(p):
     return dt.value, P.value, K.value, Kw.value
 
 
-def workspace_size(p, tile_m=0, chunk_n=0, vec=0, resident=0) -> int:
+def workspace_size(p, tile_m=0, chunk_n=0, vec=0, resident=0, wide_cols=0) -> int:
     s = to_params(p)
-    t = _tuning(tile_m, chunk_n, 0, vec, resident)
+    t = _tuning(tile_m, chunk_n, 0, vec, resident, 0, wide_cols)
     n = ctypes.c_size_t()
     _check(lib().bte_workspace_size(ctypes.byref(s), ctypes.byref(t), ctypes.byref(n)))
     return n.value
@@ -224,15 +225,18 @@ class Solver:
     ``workspace_size(p)`` bytes, e.g. from a PyTorch uint8 tensor, which the
     caller keeps alive while the solver exists.  ``resident=1`` keeps the
     grid in the shared memory of one thread-block cluster and advances it
-    with one persistent launch per step/run call (grids that fit only)."""
+    with one persistent launch per step/run call (grids that fit only);
+    ``resident=2`` is the persistent mode, ``resident=3`` the on-chip mode
+    over several clusters (``wide_cols`` phi_y columns per cluster, 0 =
+    automatic)."""
 
     def __init__(self, p, stream: int = 0, tile_m: int = 0, chunk_n: int = 0,
                  graph_steps: int = 0, workspace: int = 0, workspace_bytes: int = 0,
-                 vec: int = 0, resident: int = 0, walk: int = 0):
+                 vec: int = 0, resident: int = 0, walk: int = 0, wide_cols: int = 0):
         self._lib = lib()
         self.params = to_params(p)
         self._h = ctypes.c_void_p()
-        t = _tuning(tile_m, chunk_n, graph_steps, vec, resident, walk)
+        t = _tuning(tile_m, chunk_n, graph_steps, vec, resident, walk, wide_cols)
         _check(self._lib.bte_create_ex(ctypes.byref(self.params), ctypes.c_void_p(stream or None),
                                        ctypes.byref(t), ctypes.c_void_p(workspace or None),
                                        int(workspace_bytes), ctypes.byref(self._h)))

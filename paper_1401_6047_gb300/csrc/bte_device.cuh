@@ -181,22 +181,41 @@ __device__ __forceinline__ T stencil_b(T c, T chi, T da_prev, T da_next) {
  * equilibrium.  Each product, sum and fused multiply-add below is one
  * rounding, in this order. */
 template <typename T>
+struct CnCoef {
+    T th1, inv, ca, cb;
+};
+/* The part of the update that depends on the cell's (n, m) and the drive
+ * only, not on the state: 1/D and the two coefficients of a and b. */
+template <typename T>
+__device__ __forceinline__ CnCoef<T> cn_coef(T th, T th1, const CnK<T>& k) {
+    using O = Rn<T>;
+    CnCoef<T> c;
+    c.th1 = th1;
+    const T D = O::fma(th1, th1, k.nu2);
+    c.inv = recip<T>(D);
+    c.ca = O::fma(th1, O::add(th, th1), k.nuh);
+    c.cb = O::fma(k.xi, th1, O::mul(th, k.nu));
+    return c;
+}
+/* The rest: the new a, b from the old ones and the stencil terms. */
+template <typename T>
+__device__ __forceinline__ void cn_update(T a, T b, T Sa, T Sb, T hr, T g, const CnCoef<T>& c,
+                                          const CnK<T>& k, T& an, T& bn) {
+    using O = Rn<T>;
+    const T src = O::fma(hr, g, Sa);
+    T t = O::fma(k.nu, src, -O::mul(c.th1, Sb));
+    t = O::fma(-a, c.ca, t);
+    t = O::fma(-b, c.cb, t);
+    T u = O::fma(c.th1, src, O::mul(k.nu, Sb));
+    u = O::fma(a, c.cb, u);
+    u = O::fma(-b, c.ca, u);
+    an = O::add(a, O::mul(t, c.inv));
+    bn = O::add(b, O::mul(u, c.inv));
+}
+template <typename T>
 __device__ __forceinline__ void cn_cell(T a, T b, T Sa, T Sb, T hr, T g, T th, T th1,
                                         const CnK<T>& k, T& an, T& bn) {
-    using O = Rn<T>;
-    const T D = O::fma(th1, th1, k.nu2);
-    const T inv = recip<T>(D);
-    const T src = O::fma(hr, g, Sa);
-    const T ca = O::fma(th1, O::add(th, th1), k.nuh);
-    const T cb = O::fma(k.xi, th1, O::mul(th, k.nu));
-    T t = O::fma(k.nu, src, -O::mul(th1, Sb));
-    t = O::fma(-a, ca, t);
-    t = O::fma(-b, cb, t);
-    T u = O::fma(th1, src, O::mul(k.nu, Sb));
-    u = O::fma(a, cb, u);
-    u = O::fma(-b, ca, u);
-    an = O::add(a, O::mul(t, inv));
-    bn = O::add(b, O::mul(u, inv));
+    cn_update<T>(a, b, Sa, Sb, hr, g, cn_coef<T>(th, th1, k), k, an, bn);
 }
 
 /* The update of V consecutive columns of one row (V = 2 or 4): the stencil
@@ -256,6 +275,80 @@ __device__ __forceinline__ void cn_row(const T (&a)[V], const T (&b)[V], const T
     }
 }
 
+
+/* Split cluster barrier (all threads of every CTA of the cluster): the
+ * arrive releases this thread's earlier writes (distributed shared memory
+ * included), the wait acquires those of every thread that arrived. */
+__device__ __forceinline__ void cluster_arrive() {
+    asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+
+/* Acquire load and release store of a counter at GPU scope (completion
+ * counters that CTAs of one launch poll). */
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+/* Drive of one half-step: E and B at its start (E0, B0) and end (E1, B1),
+ * and its stencil coefficient, read from a [3][stride] drive table (E, B,
+ * coefficient; FP64 values rounded to T once on the host) at row kk. */
+template <typename T>
+struct Half {
+    T E0, E1, B0, B1, cc;
+};
+template <typename T>
+__device__ __forceinline__ Half<T> half_drive(const T* tab, int stride, int kk) {
+    Half<T> d;
+    d.E0 = tab[kk];
+    d.E1 = tab[kk + 1];
+    d.B0 = tab[stride + kk];
+    d.B1 = tab[stride + kk + 1];
+    d.cc = tab[2 * stride + kk];
+    return d;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+/* Sums of FP32 values carried as unevaluated pairs hi + lo of FP32 numbers
+ * (Knuth's error-free TwoSum, so the pair keeps about 48 bits): the per-step
+ * row sums of FP32 states need FP64-grade accuracy, and FP32 operations run
+ * at many times the rate of FP64 ones on this GPU. */
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return F2{s, e};
+}
+__device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
+    const F2 s = two_sum(x.hi, y.hi);
+    return two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+/* x + v with the pair's error term kept */
+__device__ __forceinline__ F2 f2_add1(F2 x, float v) {
+    const F2 t = two_sum(x.hi, v);
+    return F2{t.hi, __fadd_rn(x.lo, t.lo)};
+}
+__device__ __forceinline__ double warp_sum_f2(F2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = f2_add(v, F2{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)});
+    return (double)v.hi + (double)v.lo;
+}
 
 /* Sum over the block in a fixed order (warp shuffles, then warp partials
  * in warp order); the result is valid in thread 0.  `red` holds >= 32

@@ -186,11 +186,35 @@ struct Layout {
     size_t off_row_a0, off_col_g, off_col_phi, off_ew, off_ef, off_tv, off_tn, off_part,
         off_ticket, off_err, off_base, off_fin, off_res, off_done, total;
     int dring;                /* slots of the row-0 partial sums (persistent: ntx + 1) */
+    /* on chip over several clusters (resident = 3; wideG = 0 otherwise):
+     * G clusters of C CTAs, Wc columns per cluster, rp rows per CTA */
+    int wideG, wideC, wideWc, wide_rp, wide_threads;
+    size_t wide_smem;
+    size_t off_wx, off_wflag, off_wpart; /* edge columns, counters, per-cluster sums */
 };
 
 /* steps of one persistent launch at most (a bte_step/bte_run call of more
  * steps queues several launches) */
 constexpr long long kPersistMaxSteps = 8192;
+
+/* on chip over several clusters: shared memory per CTA at most, clusters
+ * at most, and the automatic choice: about 32 (FP64) or 64 (FP32) columns
+ * per cluster -- the FP64 arithmetic wants the most SMs, the FP32 steps the
+ * fewest cross-cluster exchanges (31 x 201 on a GB300: FP64 7.4 us per step
+ * with 7 clusters against 7.6 with 4; FP32 4.3 with 4 against 4.8 with 7)
+ * -- with at most 128 CTAs in all, and at create time no more clusters than
+ * fit the GPU at once */
+constexpr size_t kWideSmemMax = 232448;
+constexpr int kWideMaxClusters = 32;
+constexpr int kWideAutoCtas = 128;
+constexpr int kWideMaxThreads = 512;
+constexpr int kWideMaxCells = kWideMaxThreads - 32; /* a block's cells: one thread each, plus a warp */
+int wide_auto_cols(size_t elem) { return elem == 8 ? 32 : 64; }
+size_t wide_need(size_t elem, int rp, int Wc) {
+    return elem == 8 ? bte::wide_smem_bytes<double>(rp, Wc) : bte::wide_smem_bytes<float>(rp, Wc);
+}
+/* one thread per cell of the block, and one more warp (the row sums) */
+int wide_threads(int rp, int Wc) { return (rp * Wc + 31) / 32 * 32 + 32; }
 
 /* bytes of the on-chip mode's device record: the point's BatchInst, its
  * order entry and queue counter, and the kernel's window-sum scratch */
@@ -199,8 +223,10 @@ constexpr int kResThreads = 512; /* threads per CTA of the on-chip kernel */
 
 int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L) {
     if (t && (t->walk < 0 || t->walk > 2)) return fail(BTE_EINVAL, "tuning.walk must be 0, 1 or 2");
-    if (t && (t->resident < 0 || t->resident > 2))
-        return fail(BTE_EINVAL, "tuning.resident must be 0, 1 or 2");
+    if (t && (t->resident < 0 || t->resident > 3))
+        return fail(BTE_EINVAL, "tuning.resident must be 0, 1, 2 or 3");
+    if (t && (t->wide_cols < 0 || t->wide_cols > 4096))
+        return fail(BTE_EINVAL, "tuning.wide_cols must be in 0..4096");
     int rc = pick_tile(p, t, L.tile_m, L.chunk_n, L.vec);
     if (rc) return rc;
     L.elem = p->precision == BTE_FP64 ? 8 : 4;
@@ -227,6 +253,43 @@ int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L
         if (!L.resC)
             return fail(BTE_EINVAL, "grid %dx%d does not fit the shared memory of a 16-CTA cluster",
                         p->n_max + 1, p->m_points);
+    }
+    /* on chip over several clusters: C as for the on-chip mode (at least
+     * two rows per CTA), then Wc columns per cluster (given, or about 32
+     * with at most 128 CTAs, fewer columns while a block does not fit) */
+    L.wideG = L.wideC = L.wideWc = L.wide_rp = L.wide_threads = 0;
+    L.wide_smem = 0;
+    if (t && t->resident == 3) {
+        const int N1 = p->n_max + 1, M1 = p->m_points;
+        const int auto_cols = wide_auto_cols(L.elem);
+        auto need = [&](int rp, int Wc) { return wide_need(L.elem, rp, Wc); };
+        for (int C = 16; C >= 1 && !L.wideG; C /= 2) {
+            if (C > 1 && (N1 + C - 1) / C < 2) continue;
+            const int rp = (N1 + C - 1) / C;
+            int Wc = t->wide_cols;
+            if (!Wc) {
+                int G = std::min((M1 + auto_cols - 1) / auto_cols, std::max(1, kWideAutoCtas / C));
+                G = std::max(G, 1);
+                Wc = (M1 + G - 1) / G;
+                while ((need(rp, Wc) > kWideSmemMax || rp * Wc > kWideMaxCells) &&
+                       (M1 + Wc - 1) / Wc < kWideMaxClusters)
+                    Wc = (M1 + (M1 + Wc - 1) / Wc) / ((M1 + Wc - 1) / Wc + 1);
+            }
+            const int G = (M1 + Wc - 1) / Wc;
+            const size_t bytes = need(rp, Wc);
+            /* one cell per thread: a block of at most kWideMaxCells cells */
+            if (G > kWideMaxClusters || bytes > kWideSmemMax || rp * Wc > kWideMaxCells) continue;
+            L.wideG = G;
+            L.wideC = C;
+            L.wideWc = Wc;
+            L.wide_rp = rp;
+            L.wide_smem = bytes;
+            L.wide_threads = wide_threads(rp, Wc);
+        }
+        if (!L.wideG)
+            return fail(BTE_EINVAL,
+                        "grid %dx%d does not fit %d clusters of 16 CTAs (%zu bytes and %d cells each)",
+                        N1, M1, kWideMaxClusters, kWideSmemMax, kWideMaxCells);
     }
     L.G = (int)(128 / L.elem);
     L.H = (int)(32 / L.elem); /* halo columns the step kernel streams per side */
@@ -284,6 +347,15 @@ int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L
     o += kResBytes;
     L.off_done = o;
     o += align_up((size_t)L.ntx * L.nty * sizeof(unsigned), 256);
+    L.off_wx = L.off_wflag = L.off_wpart = o;
+    if (L.wideG) {
+        L.off_wx = o;
+        o += align_up((size_t)8 * L.wideG * N1 * L.elem, 256);
+        L.off_wflag = o;
+        o += align_up((size_t)L.wideG * L.wideC * sizeof(unsigned), 256);
+        L.off_wpart = o;
+        o += align_up((size_t)kPersistMaxSteps * L.wideG * 2 * sizeof(double), 256);
+    }
     L.total = o;
     return BTE_OK;
 }
@@ -589,6 +661,61 @@ int enqueue_resident(bte_handle* h, long long n) {
     return BTE_OK;
 }
 
+/* On chip over several clusters: launches of at most kPersistMaxSteps
+ * steps, each one launch of G clusters that advances the current ping-pong
+ * set in place (counters zeroed before it), then the fold of the
+ * per-cluster row sums into the trace. */
+template <typename T>
+int enqueue_wide(bte_handle* h, long long n) {
+    const Layout& L = h->L;
+    const int set = h->set;
+    bte::WideArgs<T> w{};
+    w.a_w = h->ptr<T>(L.off_state[4 * set + 0]);
+    w.b_w = h->ptr<T>(L.off_state[4 * set + 1]);
+    w.a_f = h->ptr<T>(L.off_state[4 * set + 2]);
+    w.b_f = h->ptr<T>(L.off_state[4 * set + 3]);
+    w.row_a0 = h->ptr<T>(L.off_row_a0);
+    w.col_g = h->ptr<T>(L.off_col_g);
+    w.col_phi = h->ptr<T>(L.off_col_phi);
+    w.e_whole = h->ptr<T>(L.off_ew);
+    w.e_frac = h->ptr<T>(L.off_ef);
+    w.xcol = h->ptr<T>(L.off_wx);
+    w.flag = h->ptr<unsigned>(L.off_wflag);
+    w.part = h->ptr<double>(L.off_wpart);
+    w.err = h->ptr<int>(L.off_err);
+    w.N = h->p.n_max;
+    w.M = h->p.m_points - 1;
+    w.pitch = L.pitch;
+    w.P = h->tg.P > 0 ? (int)h->tg.P : 0;
+    w.dstride = (h->tg.P > 0 ? (int)h->tg.P : 1) + 2;
+    w.C = L.wideC;
+    w.G = L.wideG;
+    w.Wc = L.wideWc;
+    w.rows_per = L.wide_rp;
+    const double dt = h->tg.dt_eff;
+    w.h = (T)dt;
+    w.hh = (T)(0.5 * dt);
+    w.nu = (T)(1.0 + 0.5 * dt);
+    w.xi = (T)(1.0 - 0.5 * dt);
+    const double sq = std::sqrt(h->p.alpha);
+    const double vscale = kPi * sq * h->dphi, nscale = 2.0 * kPi * sq * h->dphi;
+    while (n > 0) {
+        const long long c = n < kPersistMaxSteps ? n : kPersistMaxSteps;
+        w.K = c;
+        w.k0 = h->k;
+        CU(cudaMemsetAsync(w.flag, 0, (size_t)L.wideG * L.wideC * sizeof(unsigned), h->stream));
+        int rc = bte::launch_wide<T>(w, L.wide_threads, L.wide_smem, h->stream);
+        if (!rc)
+            rc = bte::launch_wide_fold(w.part, L.wideG, c, h->k, vscale, nscale,
+                                       h->ptr<double>(L.off_tv), h->ptr<double>(L.off_tn), h->stream);
+        if (!rc) rc = bte::launch_advance_base(h->ptr<long long>(L.off_base), c, h->stream);
+        if (rc) return fail(BTE_ECUDA, "on-chip kernel over clusters: %s", cudaGetErrorString((cudaError_t)rc));
+        h->k += c;
+        n -= c;
+    }
+    return BTE_OK;
+}
+
 /* Queues n steps: whole graphs of graph_len steps (one graph per starting
  * ping-pong set, captured on first use), then single launches.  Every launch
  * advances one step and flips the ping-pong set; launches after the first of
@@ -618,6 +745,7 @@ int enqueue_persist(bte_handle* h, long long n) {
 template <typename T>
 int enqueue_steps(bte_handle* h, long long n) {
     if (h->L.resC) return n > 0 ? enqueue_resident<T>(h, n) : BTE_OK;
+    if (h->L.wideG) return n > 0 ? enqueue_wide<T>(h, n) : BTE_OK;
     if (h->L.persist) return enqueue_persist<T>(h, n);
     while (h->graph_len >= 2 && n >= h->graph_len) {
         const int set = h->set;
@@ -1497,6 +1625,31 @@ int bte_create_ex(const bte_params* p, void* stream, const bte_tuning* tune, voi
         if (clusters < 1)
             return bail(fail(BTE_EINVAL, "a cluster of %d CTAs with %zu bytes each cannot be scheduled",
                              h->L.resC, h->L.res_smem));
+    }
+    if (h->L.wideG) {
+        /* all G clusters must be resident at once (their waits are bounded);
+         * an automatic shape takes no more clusters than fit (wider blocks:
+         * the workspace planned for the first choice still covers it) */
+        Layout& L = h->L;
+        int clusters = 0;
+        for (int attempt = 0; attempt < 4; ++attempt) {
+            rc = h->fp64 ? bte::wide_max_clusters<double>(L.wideC, L.wide_smem, L.wide_threads, &clusters)
+                         : bte::wide_max_clusters<float>(L.wideC, L.wide_smem, L.wide_threads, &clusters);
+            if (rc)
+                return bail(fail(BTE_ECUDA, "on-chip kernel configure: %s", cudaGetErrorString((cudaError_t)rc)));
+            if (clusters >= L.wideG || (tune && tune->wide_cols) || clusters < 1) break;
+            const int M1 = h->p.m_points;
+            const int Wc = (M1 + clusters - 1) / clusters;
+            const size_t bytes = wide_need(L.elem, L.wide_rp, Wc);
+            if (bytes > kWideSmemMax || L.wide_rp * Wc > kWideMaxCells) break;
+            L.wideWc = Wc;
+            L.wideG = (M1 + Wc - 1) / Wc;
+            L.wide_smem = bytes;
+            L.wide_threads = wide_threads(L.wide_rp, Wc);
+        }
+        if (clusters < L.wideG)
+            return bail(fail(BTE_EINVAL, "%d clusters of %d CTAs (%zu bytes each) do not fit the GPU at once (%d do)",
+                             L.wideG, L.wideC, L.wide_smem, clusters));
     }
     rc = h->fp64 ? upload_tables<double>(h) : upload_tables<float>(h);
     if (rc) return bail(rc);

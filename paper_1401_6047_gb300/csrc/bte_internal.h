@@ -132,6 +132,29 @@ struct ResArgs {
     size_t red_off;
 };
 
+/* Arguments of the single-instance on-chip kernel over several clusters
+ * (bte_wide.cu): G clusters of C CTAs.  Cluster g holds phi_y columns
+ * [g Wc, (g+1) Wc) of every harmonic row; CTA r of it rows [r R, (r+1) R),
+ * R = rows_per.  The state is advanced in place (one ping-pong set). */
+template <typename T>
+struct WideArgs {
+    T* a_w; T* b_w; T* a_f; T* b_f;   /* state, rows `pitch` elements apart      */
+    const T* row_a0; const T* col_g; const T* col_phi;
+    const T* e_whole; const T* e_frac; /* drive tables as in StepArgs           */
+    T* xcol;          /* [2 grids][2 sides][2 arrays][G][N+1]: each block's first
+                         (side 0) and last (side 1) column, per half-step     */
+    unsigned* flag;   /* [G C] half-steps completed in this launch, per CTA
+                         (zeroed by the caller before the launch)            */
+    double* part;     /* [K][G][2]: per-step row sums of row 0 (a) and row 1
+                         (b) of the whole grid over each cluster's columns  */
+    int* err;         /* error word: kErrTimeout when a wait gave up        */
+    long long K;      /* steps of this launch                                */
+    long long k0;     /* step index the launch starts from                   */
+    int N, M, pitch, P, dstride;
+    int C, G, Wc, rows_per;
+    T h, hh, nu, xi;
+};
+
 /* One plain application of T (start-up half step), unfused. */
 template <typename T>
 struct ApplyArgs {
@@ -202,6 +225,19 @@ template <typename T>
 int resident_max_clusters(int C, size_t smem, int threads, int* clusters);
 template <typename T>
 int launch_resident(const ResArgs<T>& a, int clusters, int threads, size_t smem, void* stream);
+/* On-chip kernel over several clusters: shared memory of one CTA, clusters
+ * of C CTAs that fit the GPU at once (sets
+ * the kernel's attributes), launch of G clusters (cooperative where the
+ * driver accepts it with clusters), and the fold of the per-cluster row
+ * sums of K steps into the trace. */
+template <typename T>
+size_t wide_smem_bytes(int rows_per, int Wc);
+template <typename T>
+int wide_max_clusters(int C, size_t smem, int threads, int* clusters);
+template <typename T>
+int launch_wide(const WideArgs<T>& a, int threads, size_t smem, void* stream);
+int launch_wide_fold(const double* part, int G, long long K, long long k0, double vscale,
+                     double nscale, double* trace_v, double* trace_n, void* stream);
 /* Sets the calling thread's bte_last_error() message; returns code. */
 int report_error(int code, const char* msg);
 template <typename T>

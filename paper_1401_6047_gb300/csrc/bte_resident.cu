@@ -38,7 +38,15 @@ namespace cg = cooperative_groups;
 namespace bte {
 namespace {
 
+using dev::cluster_arrive;
+using dev::cluster_wait;
 using dev::cn_cell;
+using dev::F2;
+using dev::Half;
+using dev::half_drive;
+using dev::two_sum;
+using dev::warp_sum;
+using dev::warp_sum_f2;
 using dev::CnK;
 using dev::Rn;
 using dev::rot_factor;
@@ -106,24 +114,6 @@ __device__ __forceinline__ void diff_ld(const T* p, T (&d)[RV<T>::V]) {
     d[V - 1] = right - own[V - 2];
 }
 
-/* Drive of one half-step: E and B at its start (E0, B0) and end (E1, B1),
- * and its stencil coefficient, read from a [3][stride] drive table (E, B,
- * coefficient; FP64 values rounded to T once on the host) at row kk. */
-template <typename T>
-struct Half {
-    T E0, E1, B0, B1, cc;
-};
-template <typename T>
-__device__ __forceinline__ Half<T> half_drive(const T* tab, int stride, int kk) {
-    Half<T> d;
-    d.E0 = tab[kk];
-    d.E1 = tab[kk + 1];
-    d.B0 = tab[stride + kk];
-    d.B1 = tab[stride + kk + 1];
-    d.cc = tab[2 * stride + kk];
-    return d;
-}
-
 /* One half-step (Sec. 3, Eqs. a_t_plus_1, b_t_plus_1, in increment form) on
  * the V cells of a group at harmonic n, in place: oA, oB the own grid's a, b;
  * da_u, da_d, db_u, db_d the phi_y differences of the other grid's a and b
@@ -167,48 +157,10 @@ __device__ __forceinline__ void cell_group(T* oA, T* oB, const T (&da_u)[RV<T>::
     }
 }
 
-/* split cluster barrier (all threads of every CTA of the cluster) */
-__device__ __forceinline__ void cluster_arrive() {
-    asm volatile("barrier.cluster.arrive.release;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_wait() {
-    asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
-}
-
 /* global array a of a point: 0 a_w, 1 b_w, 2 a_f, 3 b_f */
 template <typename T>
 __device__ __forceinline__ T* gsel(const BatchInst<T>& I, int a) {
     return a == 0 ? I.a_w[0] : a == 1 ? I.b_w[0] : a == 2 ? I.a_f[0] : I.b_f[0];
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-/* Sums of FP32 values carried as unevaluated pairs hi + lo of FP32 numbers
- * (Knuth's error-free TwoSum, so the pair keeps about 48 bits): the per-step
- * row sums of FP32 states need FP64-grade accuracy, and FP32 operations run
- * at many times the rate of FP64 ones on this GPU. */
-struct F2 {
-    float hi, lo;
-};
-__device__ __forceinline__ F2 two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return F2{s, e};
-}
-__device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
-    const F2 s = two_sum(x.hi, y.hi);
-    return two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
-}
-__device__ __forceinline__ double warp_sum_f2(F2 v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        v = f2_add(v, F2{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)});
-    return (double)v.hi + (double)v.lo;
 }
 
 template <typename T>

@@ -269,18 +269,6 @@ __device__ __forceinline__ void make_view(View<T>& v, int q, const StepArgs<T>& 
     }
 }
 
-/* Acquire load of a counter at GPU scope. */
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-/* Release store of a counter at GPU scope. */
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 /* Dependencies of item (tx, ty) before its step `target` of a persistent
  * launch: every item of the 3 x 3 block of tiles and chunks around it must
  * have completed `target` steps (it reads their rows and halo columns of

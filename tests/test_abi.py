@@ -88,7 +88,7 @@ def test_on_chip_single_instance_mode_is_planned_on_host():
     ws0, ws2 = bte.workspace_size(W.c2()), bte.workspace_size(W.c2(), resident=2)
     shape = bte.launch_shape(W.c2())
     assert ws0 < ws2 <= ws0 + 4096 * (shape["grid_x"] + 1) + 4 * shape["grid_x"] * shape["grid_y"] + 1024
-    for bad in (dict(resident=3), dict(resident=-1), dict(walk=3), dict(walk=-1)):
+    for bad in (dict(resident=4), dict(resident=-1), dict(walk=3), dict(walk=-1)):
         t = bte._tuning()
         for k, v in bad.items():
             setattr(t, k, v)
