@@ -171,7 +171,7 @@ typedef struct {
                             bits in every order.                           */
     int32_t wide_cols;   /* resident = 3: phi_y columns per cluster, 1..4096,
                             at most 32 clusters (0: automatic -- about 32
-                            columns per cluster in FP64, 64 in FP32, at
+                            columns per cluster in FP64, 128 in FP32, at
                             most 128 CTAs in all and no more clusters than
                             fit the GPU at once)                           */
 } bte_tuning;

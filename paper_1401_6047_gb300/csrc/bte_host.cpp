@@ -198,18 +198,18 @@ struct Layout {
 constexpr long long kPersistMaxSteps = 8192;
 
 /* on chip over several clusters: shared memory per CTA at most, clusters
- * at most, and the automatic choice: about 32 (FP64) or 64 (FP32) columns
+ * at most, and the automatic choice: about 32 (FP64) or 128 (FP32) columns
  * per cluster -- the FP64 arithmetic wants the most SMs, the FP32 steps the
- * fewest cross-cluster exchanges (31 x 201 on a GB300: FP64 7.4 us per step
- * with 7 clusters against 7.6 with 4; FP32 4.3 with 4 against 4.8 with 7)
- * -- with at most 128 CTAs in all, and at create time no more clusters than
- * fit the GPU at once */
+ * fewest cross-cluster exchanges (31 x 201 on a GB300: FP64 6.8-7.5 us per
+ * step with 7 clusters against 7.1-8.6 with 4; FP32 3.4-3.5 with 2 against
+ * 3.5-3.9 with 4) -- with at most 128 CTAs in all, and at create time no
+ * more clusters than fit the GPU at once */
 constexpr size_t kWideSmemMax = 232448;
 constexpr int kWideMaxClusters = 32;
 constexpr int kWideAutoCtas = 128;
 constexpr int kWideMaxThreads = 512;
 constexpr int kWideMaxCells = kWideMaxThreads - 32; /* a block's cells: one thread each, plus a warp */
-int wide_auto_cols(size_t elem) { return elem == 8 ? 32 : 64; }
+int wide_auto_cols(size_t elem) { return elem == 8 ? 32 : 128; }
 size_t wide_need(size_t elem, int rp, int Wc) {
     return elem == 8 ? bte::wide_smem_bytes<double>(rp, Wc) : bte::wide_smem_bytes<float>(rp, Wc);
 }

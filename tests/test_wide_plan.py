@@ -45,7 +45,7 @@ def plan(n1, m1, elem, cols=0):
         rp = cdiv(n1, c)
         wc = cols
         if not wc:
-            auto = 32 if elem == 8 else 64
+            auto = 32 if elem == 8 else 128
             g = max(min(cdiv(m1, auto), max(1, 128 // c)), 1)
             wc = cdiv(m1, g)
             while (wide_smem(rp, wc, elem) > SMEM_MAX or rp * wc > 480) and cdiv(m1, wc) < 32:
@@ -202,7 +202,7 @@ def test_host_plan_through_workspace_size(p, prec):
     extra = al(8 * G * (p.n_max + 1) * elem) + al(G * C * 4) + al(8192 * G * 16)
     assert bte.workspace_size(p, resident=3) == bte.workspace_size(p) + extra
     if p.n_max == 30 and p.m_points == 201:
-        assert (C, G, wc) == ((16, 7, 29) if elem == 8 else (16, 4, 51))
+        assert (C, G, wc) == ((16, 7, 29) if elem == 8 else (16, 2, 101))
 
 
 def test_rejects_bad_wide_options():
