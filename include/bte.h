@@ -147,8 +147,8 @@ typedef struct {
                             each, C as for 1) whose CTAs keep their part of
                             the four arrays in shared memory; each
                             bte_step/bte_run call is one launch per 8192
-                            steps of G x C CTAs, all resident at once (a
-                            cooperative launch), that exchange their edge
+                            steps of G x C CTAs, all resident at once
+                            (checked before the launch), that exchange their edge
                             columns through global memory behind
                             release/acquire completion counters, polled
                             with a %globaltimer bound (BTE_ETIMEOUT when a

@@ -1718,10 +1718,12 @@ int bte_observables(bte_handle* h, bte_obs* out) {
     out->steps_per_period = h->tg.P;
     out->window_steps = h->tg.Kw;
     int st = BTE_OK;
-    if (err) st = BTE_ETIMEOUT;
+    if (err == bte::kErrLaunch) st = BTE_ECUDA;
+    else if (err) st = BTE_ETIMEOUT;
     else if (fin[3] != 0.0 || !(fin[2] <= 0.05)) st = BTE_EUNSTABLE;
     out->status = st;
     out->reserved = 0;
+    if (st == BTE_ECUDA) return fail(st, "a solver kernel found itself launched in the wrong shape");
     if (st == BTE_ETIMEOUT) return fail(st, "a bounded wait in a solver kernel gave up");
     if (st == BTE_EUNSTABLE)
         return fail(st, "unstable run: |norm-1| reached %g%s", fin[2],

@@ -20,6 +20,9 @@ namespace bte {
 
 /* value stored in the device error word when a bounded wait gives up */
 constexpr int kErrTimeout = 1;
+/* ... and when a kernel finds itself launched in another shape than the
+ * one its arguments describe (it then returns before any access) */
+constexpr int kErrLaunch = 2;
 
 /* Column layout constants: G zero ghost columns before m = 0 (128 bytes),
  * H halo columns streamed on each side of a tile (16 bytes, the TMA
@@ -147,7 +150,8 @@ struct WideArgs {
                          (zeroed by the caller before the launch)            */
     double* part;     /* [K][G][2]: per-step row sums of row 0 (a) and row 1
                          (b) of the whole grid over each cluster's columns  */
-    int* err;         /* error word: kErrTimeout when a wait gave up        */
+    int* err;         /* error word: kErrTimeout when a wait gave up, kErrLaunch
+                         when the launch shape is not G clusters of C CTAs */
     long long K;      /* steps of this launch                                */
     long long k0;     /* step index the launch starts from                   */
     int N, M, pitch, P, dstride;

@@ -33,8 +33,11 @@
  * Waits on counters are bounded by %globaltimer and stop early when another
  * CTA has recorded an error; a CTA that gives up records kErrTimeout, and
  * every CTA then skips its remaining work while still passing each cluster
- * barrier (all CTAs pass the same number).  The launch asks for all G
- * clusters at once (cooperative); the host checks beforehand that they fit.
+ * barrier (all CTAs pass the same number).  The host checks before the
+ * launch that all G clusters fit the GPU at once (a plain cluster launch:
+ * a cooperative launch with clusters faulted under the profiler, whose
+ * replay did not keep the cluster shape), and the kernel checks its
+ * cluster shape before it addresses another CTA's shared memory.
  *
  * The per-cell operations are those of the streaming kernel (dev::cn_row,
  * one column per thread): FP64 cells get the same bits as there, FP32 ones
@@ -120,6 +123,13 @@ __global__ void __launch_bounds__(kWideMaxThreads) wide_kernel(WideArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     cg::cluster_group cl = cg::this_cluster();
     const int C = A.C, G = A.G, Wc = A.Wc, rp = A.rows_per;
+    /* the halo-row pushes address the CTAs of this cluster by rank: a
+     * launch in any other shape returns at once (every CTA alike, before
+     * any barrier or access) */
+    if ((int)cl.num_blocks() != C || (int)gridDim.x != G * C || gridDim.y != 1 || gridDim.z != 1) {
+        if (threadIdx.x == 0) atomicExch(A.err, kErrLaunch);
+        return;
+    }
     const int rank = (int)cl.block_rank();
     const int g = (int)blockIdx.x / C;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -363,24 +373,14 @@ int launch_wide(const WideArgs<T>& a, int threads, size_t smem, void* stream) {
     cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = (cudaStream_t)stream;
-    cudaLaunchAttribute at[2];
+    cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = a.C;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
-    at[1].id = cudaLaunchAttributeCooperative;
-    at[1].val.cooperative = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 2;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, wide_kernel<T>, a);
-    if (e != cudaSuccess) {
-        /* a driver that does not take cooperative cluster launches: all G
-         * clusters still fit at once (checked above), and every wait of the
-         * kernel is bounded */
-        (void)cudaGetLastError();
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, wide_kernel<T>, a);
-    }
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, wide_kernel<T>, a);
     return e == cudaSuccess ? 0 : (int)e;
 }
 
