@@ -123,10 +123,11 @@ __global__ void __launch_bounds__(kWideMaxThreads) wide_kernel(WideArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     cg::cluster_group cl = cg::this_cluster();
     const int C = A.C, G = A.G, Wc = A.Wc, rp = A.rows_per;
-    /* the halo-row pushes address the CTAs of this cluster by rank: a
-     * launch in any other shape returns at once (every CTA alike, before
-     * any barrier or access) */
-    if ((int)cl.num_blocks() != C || (int)gridDim.x != G * C || gridDim.y != 1 || gridDim.z != 1) {
+    /* the halo-row pushes address the CTAs of this cluster by rank, and
+     * every cell needs its thread: a launch in any other shape returns at
+     * once (every CTA alike, before any barrier or access) */
+    if ((int)cl.num_blocks() != C || (int)gridDim.x != G * C || gridDim.y != 1 || gridDim.z != 1 ||
+        (int)blockDim.x < rp * Wc + 32) {
         if (threadIdx.x == 0) atomicExch(A.err, kErrLaunch);
         return;
     }
