@@ -149,17 +149,17 @@ typedef struct {
                             bte_step/bte_run call is one launch per 8192
                             steps of G x C CTAs, all resident at once
                             (checked before the launch), that exchange their edge
-                            columns through global memory behind
-                            release/acquire completion counters, polled
-                            with a %globaltimer bound (BTE_ETIMEOUT when a
-                            wait gives up).  Per-cell arithmetic as in mode
+                            columns through global memory as words tagged
+                            with their half-step, polled with a
+                            %globaltimer bound (BTE_ETIMEOUT when a wait
+                            gives up).  Per-cell arithmetic as in mode
                             0; the per-step sums of rows 0 and 1 are added
                             per cluster, then over clusters in order.
                             One thread per cell: BTE_EINVAL when a CTA's
                             block has more than 480 cells or does not fit
                             232,448 bytes, or the G clusters do not fit the
                             GPU at once (small grids: 31 x 201 FP64 runs
-                            7.0 instead of 16.1 us per step on a GB300).
+                            5.5 instead of 16.1 us per step on a GB300).
                             0: one fused step kernel launch per step.      */
     int32_t walk;        /* order in which one-step launches walk the
                             harmonic rows of a work item: 0 automatic

@@ -190,7 +190,8 @@ struct Layout {
      * G clusters of C CTAs, Wc columns per cluster, rp rows per CTA */
     int wideG, wideC, wideWc, wide_rp, wide_threads;
     size_t wide_smem;
-    size_t off_wx, off_wflag, off_wpart; /* edge columns, counters, per-cluster sums */
+    size_t off_wx, off_wpart;  /* tagged edge-column words, per-cluster sums */
+    size_t wide_words;         /* bytes of the tagged words */
 };
 
 /* steps of one persistent launch at most (a bte_step/bte_run call of more
@@ -347,12 +348,14 @@ int plan(const bte_params* p, const bte_tuning* t, const TimeGrid& tg, Layout& L
     o += kResBytes;
     L.off_done = o;
     o += align_up((size_t)L.ntx * L.nty * sizeof(unsigned), 256);
-    L.off_wx = L.off_wflag = L.off_wpart = o;
+    L.off_wx = L.off_wpart = o;
+    L.wide_words = 0;
     if (L.wideG) {
+        /* 2 buffers x 2 grids x 2 sides x 2 arrays x (elem / 4) words of 8
+         * bytes per cluster and row */
+        L.wide_words = (size_t)16 * (L.elem / 4) * L.wideG * N1 * 8;
         L.off_wx = o;
-        o += align_up((size_t)8 * L.wideG * N1 * L.elem, 256);
-        L.off_wflag = o;
-        o += align_up((size_t)L.wideG * L.wideC * sizeof(unsigned), 256);
+        o += align_up(L.wide_words, 256);
         L.off_wpart = o;
         o += align_up((size_t)kPersistMaxSteps * L.wideG * 2 * sizeof(double), 256);
     }
@@ -679,8 +682,7 @@ int enqueue_wide(bte_handle* h, long long n) {
     w.col_phi = h->ptr<T>(L.off_col_phi);
     w.e_whole = h->ptr<T>(L.off_ew);
     w.e_frac = h->ptr<T>(L.off_ef);
-    w.xcol = h->ptr<T>(L.off_wx);
-    w.flag = h->ptr<unsigned>(L.off_wflag);
+    w.xw = h->ptr<unsigned long long>(L.off_wx);
     w.part = h->ptr<double>(L.off_wpart);
     w.err = h->ptr<int>(L.off_err);
     w.N = h->p.n_max;
@@ -703,7 +705,7 @@ int enqueue_wide(bte_handle* h, long long n) {
         const long long c = n < kPersistMaxSteps ? n : kPersistMaxSteps;
         w.K = c;
         w.k0 = h->k;
-        CU(cudaMemsetAsync(w.flag, 0, (size_t)L.wideG * L.wideC * sizeof(unsigned), h->stream));
+        CU(cudaMemsetAsync(w.xw, 0, L.wide_words, h->stream)); /* no tag left from an earlier launch */
         int rc = bte::launch_wide<T>(w, L.wide_threads, L.wide_smem, h->stream);
         if (!rc)
             rc = bte::launch_wide_fold(w.part, L.wideG, c, h->k, vscale, nscale,

@@ -144,10 +144,12 @@ struct WideArgs {
     T* a_w; T* b_w; T* a_f; T* b_f;   /* state, rows `pitch` elements apart      */
     const T* row_a0; const T* col_g; const T* col_phi;
     const T* e_whole; const T* e_frac; /* drive tables as in StepArgs           */
-    T* xcol;          /* [2 grids][2 sides][2 arrays][G][N+1]: each block's first
-                         (side 0) and last (side 1) column, per half-step     */
-    unsigned* flag;   /* [G C] half-steps completed in this launch, per CTA
-                         (zeroed by the caller before the launch)            */
+    unsigned long long* xw; /* [2 buffers][2 grids][2 sides][2 arrays][W][G][N+1]
+                         exchange words: each block's first (side 0) and last
+                         (side 1) column, the value's 32-bit part(s) (W = 1
+                         for FP32; 2 for FP64: high, low) under the number of
+                         the half-step that made it, plus one (zeroed by the
+                         caller before the launch)                           */
     double* part;     /* [K][G][2]: per-step row sums of row 0 (a) and row 1
                          (b) of the whole grid over each cluster's columns  */
     int* err;         /* error word: kErrTimeout when a wait gave up, kErrLaunch

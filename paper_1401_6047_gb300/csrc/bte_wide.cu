@@ -18,21 +18,23 @@
  *   - its first and last rows into the halo rows of the CTAs above and
  *     below it in its cluster (distributed shared memory, made visible by
  *     the split cluster barrier), and
- *   - its first and last columns into an exchange area in global memory,
- *     from which the CTAs of the neighbouring clusters fill their halo
- *     columns once the writer's completion counter (a release store at GPU
- *     scope, polled with acquire loads) shows the half-step done.
+ *   - its first and last columns into exchange words in global memory:
+ *     8-byte words, each written and read as a whole, holding 32 bits of
+ *     a value (FP64: two words) under the number of the half-step that
+ *     made it, from which the CTAs of the neighbouring clusters fill their
+ *     halo columns, polling each word until it carries the tag they expect.
+ *     A value and its tag travel together, so the exchange needs no fence,
+ *     no separate flag and no second load.
  * A CTA reads the columns of up to three CTAs on each side (the rows above
- * and below its own included: the corners of the stencil).  The counters
- * also keep a writer from overwriting an exchange slot before its readers
- * have taken it: a CTA writes a grid's columns only after it has seen each
- * of those neighbours finish the half-step before, in which they read the
- * previous values (the readers of a CTA's columns are the CTAs whose
- * columns it reads).
+ * and below its own included: the corners of the stencil).  The words come
+ * in two buffers (by the parity of the producing grid's update count), so
+ * a word is rewritten four half-steps after it was written; by then the
+ * writer has used columns that its readers made after reading it (the
+ * readers of a CTA's columns are the CTAs whose columns it reads).
  *
- * Waits on counters are bounded by %globaltimer and stop early when another
- * CTA has recorded an error; a CTA that gives up records kErrTimeout, and
- * every CTA then skips its remaining work while still passing each cluster
+ * Polls are bounded by %globaltimer and stop early when another CTA has
+ * recorded an error; a CTA that gives up records kErrTimeout, and every
+ * CTA then skips its remaining work while still passing each cluster
  * barrier (all CTAs pass the same number).  The host checks before the
  * launch that all G clusters fit the GPU at once (a plain cluster launch:
  * a cooperative launch with clusters faulted under the profiler, whose
@@ -69,10 +71,35 @@ __device__ __forceinline__ T* wsel(const WideArgs<T>& A, int a) {
     return a == 0 ? A.a_w : a == 1 ? A.b_w : a == 2 ? A.a_f : A.b_f;
 }
 
-/* exchange slot of row n: grid (0 whole, 1 fractional), side (0 first
- * column of block g, 1 last), array (0 a, 1 b) */
-__device__ __forceinline__ size_t xslot(int grid, int side, int ab, int g, int n, int G, int N1) {
-    return ((((size_t)grid * 2 + side) * 2 + ab) * G + g) * N1 + n;
+/* exchange word of row n: buffer (the parity of the producing grid's
+ * update count), grid (0 whole, 1 fractional), side (0 first column of
+ * block g, 1 last), array (0 a, 1 b), part (FP64: 0 high, 1 low half) */
+template <typename T>
+__device__ __forceinline__ size_t xword(int buf, int grid, int side, int ab, int part, int g, int n,
+                                        int G, int N1) {
+    constexpr int W = sizeof(T) / 4;
+    return ((((((size_t)buf * 2 + grid) * 2 + side) * 2 + ab) * W + part) * G + g) * N1 + n;
+}
+
+/* One 8-byte word, written and read as a whole (single-copy atomic): the
+ * tag in the high half, 32 bits of the value in the low half, so a reader
+ * that sees the tag it expects holds the value written with it. */
+__device__ __forceinline__ void st_word(unsigned long long* p, unsigned tag, unsigned bits) {
+    const unsigned long long w = ((unsigned long long)tag << 32) | bits;
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_word(const unsigned long long* p) {
+    unsigned long long w;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+    return w;
+}
+
+/* 32-bit part `part` of a value: FP32 its bits; FP64 part 0 the high half,
+ * part 1 the low half */
+__device__ __forceinline__ unsigned val_part(float v, int) { return __float_as_uint(v); }
+__device__ __forceinline__ unsigned val_part(double v, int part) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return part == 0 ? (unsigned)(b >> 32) : (unsigned)b;
 }
 
 /* A thread's part of a row sum: FP64 for FP64 states, an error-free pair
@@ -91,31 +118,6 @@ struct RowSum<float> {
     __device__ __forceinline__ void add(float x) { v = f2_add1(v, x); }
     __device__ __forceinline__ double warp() const { return warp_sum_f2(v); }
 };
-
-/* Warp 0: wait until every CTA whose columns this CTA reads has completed
- * `target` half-steps.  Lane i < 6 polls CTA rank + i % 3 - 1 (kept within
- * [rank_lo, rank_hi], the ranks holding rows r0 - 1 .. r1) of cluster g - 1
- * (i < 3) or g + 1.  False on every lane when the wait gave up (2 s of
- * %globaltimer) or another CTA recorded an error. */
-__device__ __forceinline__ bool wait_columns(const unsigned* flag, int g, int G, int C, int rank,
-                                             int rank_lo, int rank_hi, unsigned target,
-                                             const int* err) {
-    const int lane = threadIdx.x & 31;
-    const int gg = lane < 3 ? g - 1 : g + 1;
-    const int rr = rank + lane % 3 - 1;
-    const bool mine = lane < 6 && gg >= 0 && gg < G && rr >= rank_lo && rr <= rank_hi;
-    const unsigned* c = flag + (mine ? gg * C + rr : 0);
-    bool ready = !mine || ld_acquire(c) >= target;
-    if (__all_sync(0xffffffffu, ready)) return true;
-    const uint64_t t0 = global_timer();
-    for (;;) {
-        if (!ready) ready = ld_acquire(c) >= target;
-        if (__all_sync(0xffffffffu, ready)) return true;
-        const bool stop = *reinterpret_cast<const volatile int*>(err) != 0 ||
-                          global_timer() - t0 > kWaitLimitNs;
-        if (__any_sync(0xffffffffu, stop)) return false;
-    }
-}
 
 template <typename T>
 __global__ void __launch_bounds__(kWideMaxThreads) wide_kernel(WideArgs<T> A) {
@@ -231,24 +233,41 @@ __global__ void __launch_bounds__(kWideMaxThreads) wide_kernel(WideArgs<T> A) {
             }
             cluster_wait(); /* halo rows of grid x pushed by the cluster's CTAs */
             if (G > 1 && hs > 0) {
-                /* warp 0 waits for the neighbouring clusters' counters, then
-                 * fills the halo columns of grid x (shared rows 0 .. R+1:
-                 * the left one is block g-1's last column, the right one
-                 * block g+1's first) */
-                bool gave_up = dead;
-                if (warp == 0 && !dead) {
-                    gave_up = !wait_columns(A.flag, g, G, C, rank, rank_lo, rank_hi, hs, A.err);
-                    __syncwarp(); /* each lane's acquire, before every lane's loads */
-                    if (!gave_up)
-                        for (int q = lane; q < 4 * (R + 2); q += 32) {
-                            const int side = q & 1, ab = (q >> 1) & 1, li = q >> 2;
-                            const int nq = r0 - 1 + li, gg = side ? g + 1 : g - 1;
-                            if (nq < 0 || nq > N || gg < 0 || gg >= G) continue;
-                            s[(size_t)(x + ab) * arr + (size_t)li * Wp + (side ? Wc + 1 : 0)] =
-                                __ldcg(A.xcol + xslot(x >> 1, side ? 0 : 1, ab, gg, nq, G, N1));
+                /* warp 0 fills the halo columns of grid x (shared rows
+                 * 0 .. R+1; the left one is block g-1's last column, the
+                 * right one block g+1's first) from the exchange words
+                 * that the neighbouring clusters wrote in half-step hs-1,
+                 * polling each until it carries tag hs (bounded by
+                 * %globaltimer; given up at once once an error is recorded) */
+                bool ok = !dead;
+                if (warp == 0 && ok) {
+                    constexpr int W = sizeof(T) / 4;
+                    const int buf = ((hs - 1) >> 1) & 1;
+                    const uint64_t t0 = global_timer();
+                    for (int q = lane; q < 4 * W * (R + 2) && ok; q += 32) {
+                        const int side = q & 1, ab = (q >> 1) & 1, part = (q >> 2) % W;
+                        const int li = q / (4 * W);
+                        const int nq = r0 - 1 + li, gg = side ? g + 1 : g - 1;
+                        if (nq < 0 || nq > N || gg < 0 || gg >= G) continue;
+                        const unsigned long long* p =
+                            A.xw + xword<T>(buf, x >> 1, side ? 0 : 1, ab, part, gg, nq, G, N1);
+                        unsigned long long w = ld_word(p);
+                        while ((unsigned)(w >> 32) != hs) {
+                            if (*reinterpret_cast<const volatile int*>(A.err) != 0 ||
+                                global_timer() - t0 > kWaitLimitNs) {
+                                ok = false;
+                                break;
+                            }
+                            w = ld_word(p);
                         }
+                        /* the value's 32-bit part into its place in the halo
+                         * cell (FP64: the high half at the higher address) */
+                        T* cellp = s + (size_t)(x + ab) * arr + (size_t)li * Wp + (side ? Wc + 1 : 0);
+                        reinterpret_cast<unsigned*>(cellp)[W == 2 && part == 0 ? 1 : 0] = (unsigned)w;
+                    }
+                    ok = __all_sync(0xffffffffu, ok);
                 }
-                if (__syncthreads_or(gave_up)) {
+                if (__syncthreads_or(!ok)) {
                     if (!dead && tid == 0) atomicExch(A.err, kErrTimeout);
                     dead = true;
                 }
@@ -279,13 +298,23 @@ __global__ void __launch_bounds__(kWideMaxThreads) wide_kernel(WideArgs<T> A) {
                     halo_dn[(size_t)o * arr + lc] = na;
                     halo_dn[(size_t)(o + 1) * arr + lc] = nb;
                 }
-                if (j == 0 && g > 0) {
-                    __stcg(A.xcol + xslot(o >> 1, 0, 0, g, n, G, N1), na);
-                    __stcg(A.xcol + xslot(o >> 1, 0, 1, g, n, G, N1), nb);
-                }
-                if (j == Wc - 1 && g + 1 < G) {
-                    __stcg(A.xcol + xslot(o >> 1, 1, 0, g, n, G, N1), na);
-                    __stcg(A.xcol + xslot(o >> 1, 1, 1, g, n, G, N1), nb);
+                /* a first (side 0) or last (side 1) column that a
+                 * neighbouring cluster reads: tagged words, tag hs + 1 */
+                const bool w_first = j == 0 && g > 0, w_last = j == Wc - 1 && g + 1 < G;
+                if (w_first || w_last) {
+                    constexpr int W = sizeof(T) / 4;
+                    const int buf = (hs >> 1) & 1;
+#pragma unroll
+                    for (int sd = 0; sd < 2; ++sd) {
+                        if (!(sd == 0 ? w_first : w_last)) continue;
+#pragma unroll
+                        for (int part = 0; part < W; ++part) {
+                            st_word(A.xw + xword<T>(buf, o >> 1, sd, 0, part, g, n, G, N1), hs + 1,
+                                    val_part(na, part));
+                            st_word(A.xw + xword<T>(buf, o >> 1, sd, 1, part, g, n, G, N1), hs + 1,
+                                    val_part(nb, part));
+                        }
+                    }
                 }
             }
             /* the next half-step's drive and coefficients, computed while
@@ -295,9 +324,6 @@ __global__ void __launch_bounds__(kWideMaxThreads) wide_kernel(WideArgs<T> A) {
             cf = coef(D);
             __syncthreads();
             cluster_arrive();
-            /* the block's stores of the half-step, ordered before the
-             * counter by the barrier and the release */
-            if (G > 1 && !dead && tid == 0) st_release(A.flag + blockIdx.x, hs + 1);
         }
         if (A.P > 0 && ++kk == A.P) kk = 0; /* P = 0 (omega = 0): row 0 every step */
     }

@@ -1,7 +1,7 @@
 """On-chip mode over several clusters (bte_tuning.resident = 3): the grid
 cut into column blocks, one thread-block cluster each, CTAs holding their
 part of the four arrays in shared memory for a whole call and exchanging
-edge columns through global memory behind completion counters.
+edge columns through global memory as words tagged with their half-step.
 
 Per cell the kernel performs the operations of the one-launch-per-step
 mode in the same order: FP64 states come out bit for bit the same, FP32
@@ -112,11 +112,12 @@ def test_wide_matches_single_cluster_on_chip_mode():
 
 
 def test_wide_abort_after_recorded_error_and_reset():
-    """With an error already recorded (a bounded wait that ran out), a
-    counter wait that has to poll gives up at once, its CTA skips the rest
-    of its work while still passing each cluster barrier, and the CTAs that
-    wait on it give up in turn: the launch ends, the call reports
-    BTE_ETIMEOUT, and a reset gives the same results as a fresh run."""
+    """With an error already recorded (a bounded wait that ran out), a poll
+    of an exchange word that has to wait gives up at once, its CTA skips
+    the rest of its work while still passing each cluster barrier, and the
+    CTAs that poll its words give up in turn: the launch ends, the call
+    reports BTE_ETIMEOUT, and a reset gives the same results as a fresh
+    run."""
     p = _params(30, 201, W.FP64, periods=1.0)
     with bte.Solver(p, resident=3, wide_cols=32) as s:
         s.run()

@@ -7,17 +7,16 @@ values of the other grid a half-step reads (rows n-1 and n+1 at columns
 m-1 and m+1), and where each of them comes from -- the CTA's own cells,
 the halo rows that the CTAs above and below push (their first or last own
 row), or the halo columns filled from the exchange area that CTAs of the
-neighbouring clusters write (their first or last own column).  The checks:
-every cell is owned exactly once; every value read comes from the CTA that
-makes it, through a slot that writer fills and this reader reads; the
-reader waits on that writer's counter; every reader of a CTA's slots is a
-CTA it waits on (so slots are not overwritten before they are read); and
-every shared-memory and exchange index is in bounds.  The host's automatic
-choice of the launch shape is mirrored too and pinned through the
-workspace size the library reports.
+neighbouring clusters write (their first or last own column) as tagged
+exchange words.  The checks: every cell is owned exactly once; every value
+read comes from the CTA that makes it, through a word that writer fills and
+this reader polls (the lane mapping of the kernel's warp 0 covers each word
+read); every reader of a CTA's words is a CTA whose words it polls (so a
+word is not rewritten before it is read); and every shared-memory and
+exchange index is in bounds.  The host's automatic choice of the launch
+shape is mirrored too and pinned through the workspace size the library
+reports.
 """
-import itertools
-
 import pytest
 
 from paper_1401_6047_gb300 import bte
@@ -68,19 +67,10 @@ class Cta:
         self.c0 = g * wc
         self.have_up = self.R > 0 and self.r0 >= 1
         self.have_dn = self.R > 0 and self.r1 <= N
-        self.rank_lo = rank - 1 if self.have_up else rank
-        self.rank_hi = rank + 1 if self.have_dn else rank
-        # lanes of wait_columns
-        self.waits = set()
-        for lane in range(32):
-            gg = g - 1 if lane < 3 else g + 1
-            rr = rank + lane % 3 - 1
-            if lane < 6 and 0 <= gg < G and self.rank_lo <= rr <= self.rank_hi:
-                self.waits.add((gg, rr))
 
 
-def xslot(grid, side, ab, g, n, G, n1):
-    return (((grid * 2 + side) * 2 + ab) * G + g) * n1 + n
+def xword(buf, grid, side, ab, part, g, n, G, n1, W):
+    return ((((((buf * 2 + grid) * 2 + side) * 2 + ab) * W + part) * G + g) * n1 + n)
 
 
 SHAPES = [
@@ -98,7 +88,9 @@ SHAPES = [
 
 
 @pytest.mark.parametrize("shape", SHAPES)
-def test_partition_exchange_and_waits(shape):
+@pytest.mark.parametrize("W", [1, 2])  # 32-bit parts per value: FP32, FP64
+@pytest.mark.parametrize("hs", [0, 1, 2, 3])  # the half-step that writes
+def test_partition_exchange_and_waits(shape, W, hs):
     N, M, cols = shape
     n1, m1 = N + 1, M + 1
     C, G, wc, rp = plan(n1, m1, 4, cols)
@@ -116,7 +108,8 @@ def test_partition_exchange_and_waits(shape):
 
     wp = wc + 2
     arr = (rp + 2) * wp
-    nslots = 8 * G * n1
+    nslots = 16 * W * G * n1
+    buf = (hs >> 1) & 1  # the writer's buffer, the one its readers poll at hs + 1
     # writes of one half-step: DSMEM pushes (target CTA, shared index) and
     # exchange slots, by the cell rule of the kernel
     pushes, slots = {}, {}
@@ -136,15 +129,16 @@ def test_partition_exchange_and_waits(shape):
                             idx = (o + ab) * arr + lc
                             assert 0 <= idx < 4 * arr
                             pushes[((g, r + 1), idx)] = (n, t.c0 + j)
-                        if j == 0 and g > 0:
-                            k = xslot(o >> 1, 0, ab, g, n, G, n1)
-                            assert 0 <= k < nslots and (k not in slots or slots[k][0] == (g, r))
-                            slots[k] = ((g, r), (n, t.c0))
-                        if j == wc - 1 and g + 1 < G:
-                            k = xslot(o >> 1, 1, ab, g, n, G, n1)
-                            assert 0 <= k < nslots and (k not in slots or slots[k][0] == (g, r))
-                            slots[k] = ((g, r), (n, t.c0 + j))
-    readers = {}
+                        for part in range(W):
+                            if j == 0 and g > 0:
+                                k = xword(buf, o >> 1, 0, ab, part, g, n, G, n1, W)
+                                assert 0 <= k < nslots and (k not in slots or slots[k][0] == (g, r))
+                                slots[k] = ((g, r), (n, t.c0))
+                            if j == wc - 1 and g + 1 < G:
+                                k = xword(buf, o >> 1, 1, ab, part, g, n, G, n1, W)
+                                assert 0 <= k < nslots and (k not in slots or slots[k][0] == (g, r))
+                                slots[k] = ((g, r), (n, t.c0 + j))
+    readers, polls = {}, {}
     for (g, r), t in ctas.items():
         if t.R == 0:
             continue
@@ -167,25 +161,35 @@ def test_partition_exchange_and_waits(shape):
                                 assert pushes[((g, r), o * arr + li * wp + lc)] == (n, m)
                             assert src == (g, r - 1 if li == 0 else r + 1)
                         else:
-                            # halo column from the exchange area
+                            # halo column from the exchange words, polled by
+                            # the kernel's lane mapping of warp 0
                             side = 0 if lc == wc + 1 else 1
                             gg = g + 1 if lc == wc + 1 else g - 1
+                            polled = set()
+                            for q in range(4 * W * (t.R + 2)):
+                                qs, qab, qpart, qli = q & 1, (q >> 1) & 1, (q >> 2) % W, q // (4 * W)
+                                qn, qg = t.r0 - 1 + qli, (g + 1 if qs else g - 1)
+                                if 0 <= qn <= N and 0 <= qg < G:
+                                    polled.add((qs ^ 1, qab, qpart, qg, qn, qli, (wc + 1) if qs else 0))
                             for grid in (0, 1):
-                                k = xslot(grid, side, 0, gg, n, G, n1)
-                                assert slots[k] == (src, (n, m))
-                                readers.setdefault(src, set()).add((g, r))
-                            assert src in t.waits, "the reader waits on the writer's counter"
+                                for ab in (0, 1):
+                                    for part in range(W):
+                                        assert (side, ab, part, gg, n, li, lc) in polled
+                                        k = xword(buf, grid, side, ab, part, gg, n, G, n1, W)
+                                        assert slots[k] == (src, (n, m))
+                            readers.setdefault(src, set()).add((g, r))
+                            polls.setdefault((g, r), set()).add(src)
     for w, rs in readers.items():
         for rd in rs:
-            assert rd in ctas[w].waits, "a writer waits on each reader of its slots"
+            assert rd in polls.get(w, set()), "a writer polls the words of each reader of its words"
 
 
 @pytest.mark.parametrize("p,prec", [
     (W.c1_fp64(), W.FP64), (W.c1_fp64(), W.FP32_MIXED), (W.c2(W.FP32_MIXED), W.FP32_MIXED),
     (W.paper_table1(W.FP32_MIXED), W.FP32_MIXED)])
 def test_host_plan_through_workspace_size(p, prec):
-    """The workspace of mode 3 is that of mode 0 plus the edge-column
-    exchange area, the counters and the per-cluster sums of 8192 steps, for
+    """The workspace of mode 3 is that of mode 0 plus the tagged edge-column
+    words (two buffers) and the per-cluster sums of 8192 steps, for
     the (C, G) the mirrored plan picks; grids that need more than 480 cells
     per CTA in 32 clusters (401 x 4001, 120 x 4000) are refused."""
     p = p.replace(precision=prec)
@@ -199,7 +203,7 @@ def test_host_plan_through_workspace_size(p, prec):
         return
     C, G, wc, rp = pl
     al = lambda x: cdiv(x, 256) * 256
-    extra = al(8 * G * (p.n_max + 1) * elem) + al(G * C * 4) + al(8192 * G * 16)
+    extra = al(16 * (elem // 4) * G * (p.n_max + 1) * 8) + al(8192 * G * 16)
     assert bte.workspace_size(p, resident=3) == bte.workspace_size(p) + extra
     if p.n_max == 30 and p.m_points == 201:
         assert (C, G, wc) == ((16, 7, 29) if elem == 8 else (16, 2, 101))
