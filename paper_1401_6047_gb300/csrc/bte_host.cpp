@@ -208,8 +208,7 @@ constexpr long long kPersistMaxSteps = 8192;
 constexpr size_t kWideSmemMax = 232448;
 constexpr int kWideMaxClusters = 32;
 constexpr int kWideAutoCtas = 128;
-constexpr int kWideMaxThreads = 512;
-constexpr int kWideMaxCells = kWideMaxThreads - 32; /* a block's cells: one thread each, plus a warp */
+constexpr int kWideMaxCells = bte::kWideMaxThreads - 32; /* a block's cells: one thread each, plus a warp */
 int wide_auto_cols(size_t elem) { return elem == 8 ? 32 : 128; }
 size_t wide_need(size_t elem, int rp, int Wc) {
     return elem == 8 ? bte::wide_smem_bytes<double>(rp, Wc) : bte::wide_smem_bytes<float>(rp, Wc);

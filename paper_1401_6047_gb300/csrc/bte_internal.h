@@ -135,6 +135,9 @@ struct ResArgs {
     size_t red_off;
 };
 
+/* threads per CTA of the on-chip kernel over several clusters, at most */
+constexpr int kWideMaxThreads = 512;
+
 /* Arguments of the single-instance on-chip kernel over several clusters
  * (bte_wide.cu): G clusters of C CTAs.  Cluster g holds phi_y columns
  * [g Wc, (g+1) Wc) of every harmonic row; CTA r of it rows [r R, (r+1) R),

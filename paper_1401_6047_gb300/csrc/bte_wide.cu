@@ -63,8 +63,6 @@ namespace {
 
 using namespace dev;
 
-constexpr int kWideMaxThreads = 512;
-
 /* global array a: 0 a_w, 1 b_w, 2 a_f, 3 b_f */
 template <typename T>
 __device__ __forceinline__ T* wsel(const WideArgs<T>& A, int a) {
