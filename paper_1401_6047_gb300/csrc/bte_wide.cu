@@ -392,7 +392,7 @@ int launch_wide(const WideArgs<T>& a, int threads, size_t smem, void* stream) {
     int fit = 0;
     int rc = wide_max_clusters<T>(a.C, smem, threads, &fit); /* attributes are per function */
     if (rc) return rc;
-    if (fit < a.G) return (int)cudaErrorCooperativeLaunchTooLarge;
+    if (fit < a.G) return (int)cudaErrorLaunchOutOfResources; /* the G clusters do not fit at once */
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(a.G * a.C, 1, 1);
     cfg.blockDim = dim3(threads, 1, 1);
